@@ -1,0 +1,217 @@
+"""Seeded synthetic relations for n-way equi-join workloads.
+
+This module only draws random numbers and lays them out as columnar tables.
+It holds none of the join method's arithmetic, so that both the CPU oracle
+and the CUDA path can take identical inputs from it.
+
+The paper evaluates on JOB, TPC-H and lastFM queries (Section 4, "Data" and
+"Queries"); those datasets are not used here.  The generators below produce
+stand-ins with the shapes the paper's many-to-many workloads have: chain and
+star joins whose join attributes are skewed (Zipf) or uniform, tables with
+duplicate key tuples (bag semantics, Figure 1), and key values that die
+between joins (unneeded intermediate results, Section 1.1).
+
+Conventions
+-----------
+* A relation is a set of int32 key columns, each bound to an attribute id,
+  plus payload columns (int32 or int64) that are carried through the join.
+* Two relations join on every attribute id they share.
+* A query lists its relations with the root first.
+* Zipf(s, D): rank r in [0, D) drawn with probability proportional to
+  (r+1)^-s by inverse-CDF lookup; s = 0 is uniform.  The key value is a
+  seeded random permutation of the rank, drawn separately for every
+  (relation, column), so heavy hitters of different tables do not line up.
+  ``aligned=True`` skips the permutation (key = rank), which makes heavy
+  hitters coincide and is used to build joins whose size exceeds 2^64.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20261203
+
+
+@dataclass
+class Relation:
+    name: str
+    attrs: list            # attribute id per key column
+    keys: list             # np.int32[n] per key column
+    payloads: list = field(default_factory=list)   # np.int32[n] or np.int64[n]
+
+    @property
+    def n_rows(self) -> int:
+        if self.keys:
+            return int(self.keys[0].shape[0])
+        if self.payloads:
+            return int(self.payloads[0].shape[0])
+        return 0
+
+
+@dataclass
+class Query:
+    name: str
+    relations: list        # relations[0] is the root
+    attr_names: dict = field(default_factory=dict)
+
+    @property
+    def n_rows_total(self) -> int:
+        return sum(r.n_rows for r in self.relations)
+
+
+_CDF_CACHE: dict = {}
+
+
+def _zipf_cdf(s: float, D: int) -> np.ndarray:
+    key = (float(s), int(D))
+    cdf = _CDF_CACHE.get(key)
+    if cdf is None:
+        p = np.arange(1, D + 1, dtype=np.float64) ** (-float(s))
+        cdf = np.cumsum(p)
+        cdf /= cdf[-1]
+        _CDF_CACHE.clear()
+        _CDF_CACHE[key] = cdf
+    return cdf
+
+
+def zipf_ranks(rng: np.random.Generator, n: int, s: float, D: int) -> np.ndarray:
+    """n ranks in [0, D) with P(r) proportional to (r+1)^-s (uniform if s == 0)."""
+    if n == 0:
+        return np.zeros(0, dtype=np.int64)
+    if s == 0.0:
+        return rng.integers(0, D, size=n, dtype=np.int64)
+    cdf = _zipf_cdf(s, D)
+    u = rng.random(n)
+    r = np.searchsorted(cdf, u, side="right")
+    np.minimum(r, D - 1, out=r)
+    return r
+
+
+def zipf_keys(rng: np.random.Generator, n: int, s: float, D: int,
+              aligned: bool = False) -> np.ndarray:
+    r = zipf_ranks(rng, n, s, D)
+    if aligned or s == 0.0:
+        return r.astype(np.int32)
+    perm = rng.permutation(D).astype(np.int32)
+    return perm[r]
+
+
+def _payload(rng: np.random.Generator, n: int, dtype) -> np.ndarray:
+    info = np.iinfo(dtype)
+    return rng.integers(info.min, info.max, size=n, dtype=dtype, endpoint=True)
+
+
+def chain_query(name: str, rows, domains, s, payload_dtype, seed: int,
+                aligned: bool = False) -> Query:
+    """Chain R_1(K_0,K_1) join R_2(K_1,K_2) join ... join R_k(K_{k-1},K_k).
+
+    rows[i] is |R_{i+1}|; domains[j] and s[j] are the domain size and Zipf
+    exponent of attribute K_j (len k+1).
+    """
+    k = len(rows)
+    assert len(domains) == k + 1 and len(s) == k + 1
+    rng = np.random.default_rng(seed)
+    rels = []
+    for i in range(k):
+        n = int(rows[i])
+        cols = [zipf_keys(rng, n, s[i], int(domains[i]), aligned),
+                zipf_keys(rng, n, s[i + 1], int(domains[i + 1]), aligned)]
+        pays = [_payload(rng, n, payload_dtype)] if payload_dtype is not None else []
+        rels.append(Relation(f"R{i + 1}", [i, i + 1], cols, pays))
+    names = {j: f"K{j}" for j in range(k + 1)}
+    return Query(name, rels, names)
+
+
+def chain3_uniform(seed: int = SEED_BASE + 0, rows: int = 10**4,
+                   end_domain: int = 10**4, mid_domain: int = 1000) -> Query:
+    """R1(A,B) join R2(B,C) join R3(C,D): A, D uniform over [0, end_domain),
+    B, C uniform over [0, mid_domain), one int32 payload per table."""
+    q = chain_query("chain3_uniform", [rows] * 3,
+                    [end_domain, mid_domain, mid_domain, end_domain],
+                    [0.0] * 4, np.int32, seed)
+    q.attr_names = {0: "A", 1: "B", 2: "C", 3: "D"}
+    return q
+
+
+def chain5_zipf(seed: int = SEED_BASE + 1, rows: int = 10**7, domain: int = 10**6,
+                s: float = 1.1, aligned: bool = False) -> Query:
+    """R_i(K_{i-1},K_i), i = 1..5, Zipf(s) keys over [0, domain), one int64
+    payload per table."""
+    return chain_query("chain5_zipf", [rows] * 5, [domain] * 6, [s] * 6,
+                       np.int64, seed, aligned)
+
+
+def star_poisson(seed: int = SEED_BASE + 2, fact_rows: int = 10**8, domain: int = 10**6,
+                 n_dims: int = 4, lam: float = 2.0) -> Query:
+    """Fact F(K_1..K_n, P) with K_j uniform over [0, domain), joined to
+    dimension tables D_j(K_j, P_j) that hold Poisson(lam) copies of every key
+    in [0, domain), shuffled.  int64 payloads."""
+    rng = np.random.default_rng(seed)
+    fk = [rng.integers(0, domain, size=fact_rows, dtype=np.int32) for _ in range(n_dims)]
+    fact = Relation("F", list(range(1, n_dims + 1)), fk,
+                    [_payload(rng, fact_rows, np.int64)])
+    rels = [fact]
+    for j in range(1, n_dims + 1):
+        reps = rng.poisson(lam, size=domain)
+        keys = np.repeat(np.arange(domain, dtype=np.int32), reps)
+        rng.shuffle(keys)
+        rels.append(Relation(f"D{j}", [j], [keys],
+                             [_payload(rng, keys.shape[0], np.int64)]))
+    names = {j: f"K{j}" for j in range(1, n_dims + 1)}
+    return Query("star_poisson", rels, names)
+
+
+def batch_queries(seed: int = SEED_BASE + 3, n_queries: int = 4096,
+                  min_tables: int = 3, max_tables: int = 6,
+                  rows_range=(10**3, 10**6), domain_range=(10**2, 10**5),
+                  s_range=(0.0, 1.5)) -> list:
+    """Independent chain joins: tables per query uniform in [min,max], rows
+    per table and domain per attribute log-uniform, one Zipf exponent per
+    query uniform in s_range; int32 keys, no payloads."""
+    rng = np.random.default_rng(seed)
+    out = []
+    lo_r, hi_r = np.log(rows_range[0]), np.log(rows_range[1])
+    lo_d, hi_d = np.log(domain_range[0]), np.log(domain_range[1])
+    for qi in range(n_queries):
+        k = int(rng.integers(min_tables, max_tables + 1))
+        rows = np.exp(rng.uniform(lo_r, hi_r, size=k)).astype(np.int64)
+        doms = np.exp(rng.uniform(lo_d, hi_d, size=k + 1)).astype(np.int64)
+        s = float(rng.uniform(*s_range))
+        sub = int(rng.integers(0, 2**62))
+        out.append(chain_query(f"batch{qi}", rows, doms, [s] * (k + 1), None, sub))
+    return out
+
+
+def random_tree_query(seed: int, n_rel: int, max_rows: int = 6, domain: int = 3,
+                      max_new: int = 2, payload: bool = True, min_rows: int = 0) -> Query:
+    """Small random acyclic query: relation j > 0 attaches to a random earlier
+    relation, shares one attribute of it, and adds 0..max_new attributes of
+    its own.  Values are uniform over a small domain so that joins match,
+    repeat and die."""
+    rng = np.random.default_rng(seed)
+    next_attr = 0
+    rel_attrs = []
+    for j in range(n_rel):
+        if j == 0:
+            na = int(rng.integers(1, max_new + 2))
+            attrs = list(range(next_attr, next_attr + na))
+            next_attr += na
+        else:
+            par = int(rng.integers(0, j))
+            shared = int(rng.choice(rel_attrs[par]))
+            na = int(rng.integers(0, max_new + 1))
+            new = list(range(next_attr, next_attr + na))
+            next_attr += na
+            attrs = [shared] + new
+            rng.shuffle(attrs)
+        rel_attrs.append([int(a) for a in attrs])
+    rels = []
+    for j, attrs in enumerate(rel_attrs):
+        n = int(rng.integers(min_rows, max_rows + 1))
+        cols = [rng.integers(-1, domain - 1, size=n, dtype=np.int32) for _ in attrs]
+        pays = []
+        if payload:
+            pays = [_payload(rng, n, np.int32), _payload(rng, n, np.int64)]
+        rels.append(Relation(f"T{j}", attrs, cols, pays))
+    return Query(f"tree{seed}", rels, {a: f"X{a}" for a in range(next_attr)})

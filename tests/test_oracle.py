@@ -1,0 +1,290 @@
+"""Pins the CPU oracle to facts fixed outside itself: the paper's worked
+example (Figures 1 and 2, Section 1.1), brute-force nested loops over every
+row combination on tiny inputs, closed forms, and the 2^64 boundary."""
+import itertools
+from collections import Counter
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_10435_gb300 import datagen as G
+from tests import golden_fig
+
+CAP = (1 << 64) - 1
+
+
+# ------------------------------------------------------------------ helpers
+
+def brute_force(q):
+    """All row-id tuples whose rows agree on every shared attribute (the
+    definition of the natural join, checked pairwise over ALL relations,
+    not along a tree)."""
+    rels = q.relations
+    k = len(rels)
+    pairs = []
+    for i in range(k):
+        for j in range(i + 1, k):
+            for ci, a in enumerate(rels[i].attrs):
+                if a in rels[j].attrs:
+                    pairs.append((i, ci, j, rels[j].attrs.index(a)))
+    out = []
+    for combo in itertools.product(*[range(R.n_rows) for R in rels]):
+        if all(rels[i].keys[ci][combo[i]] == rels[j].keys[cj][combo[j]]
+               for i, ci, j, cj in pairs):
+            out.append(combo)
+    return out
+
+
+def value_of(q, combo, attr):
+    for j, R in enumerate(q.relations):
+        if attr in R.attrs:
+            return int(R.keys[R.attrs.index(attr)][combo[j]])
+    raise KeyError(attr)
+
+
+def canonical(q, tuples, V):
+    return sorted(tuples, key=lambda t: tuple(value_of(q, t, a) for a in V) + tuple(t))
+
+
+def levels_by_definition(q, tuples, V):
+    """Per-prefix runs of the sorted result (Def. 1 / Algorithm 4)."""
+    out = []
+    for l in range(len(V)):
+        runs = []
+        prev = None
+        for i, t in enumerate(tuples):
+            pre = tuple(value_of(q, t, a) for a in V[:l + 1])
+            if pre != prev:
+                runs.append([pre[-1], 0, i])
+                prev = pre
+            runs[-1][1] += 1
+        out.append(runs)
+    return out
+
+
+def tiny_queries():
+    qs = []
+    for seed in range(160):
+        n_rel = 1 + seed % 5
+        qs.append(G.random_tree_query(seed, n_rel, max_rows=5 if n_rel <= 3 else 4,
+                                      domain=3 if n_rel <= 2 else 2, max_new=2,
+                                      min_rows=0 if seed % 7 == 0 else 1))
+    return qs
+
+
+# ------------------------------------------------------------------ Figure 1 / 2
+
+def test_figure1_plan_is_chain_rooted_at_A():
+    q, *_ = golden_fig.load()
+    pl = O.plan(q)
+    assert pl.parent == [-1, 0, 1]
+    assert pl.V == [0, 1, 2, 3]          # A, B, C, D (root A, Section 3.3 example)
+
+
+def test_figure1_join_size_and_result():
+    q, result, _, _ = golden_fig.load()
+    c = O.count(q)
+    assert c.total == 32 and not c.overflow
+    j = O.join(q)
+    cols = O.columns(q, j.rowids)
+    got = list(zip(*[c_.tolist() for c_ in cols]))
+    assert got == result                  # Figure 2, rows 0..31
+
+
+def test_figure1_gfjs_levels():
+    q, _, gfjs, _ = golden_fig.load()
+    j = O.join(q)
+    lv = O.gfjs_levels(q, j.rowids)
+    for l, name in enumerate("ABCD"):
+        assert list(zip(lv[l].value.tolist(), lv[l].freq.tolist())) == gfjs[name]
+        assert int(lv[l].freq.sum()) == 32          # equal sums per column (Def. 1)
+        off = np.concatenate([[0], np.cumsum(lv[l].freq)[:-1]])
+        assert (lv[l].offset == off).all()
+
+
+def test_figure1_unneeded_intermediate_tuples():
+    q, _, _, facts = golden_fig.load()
+    j = O.join(q)
+    # the cascade joins T1 with T2 first; tuples of that intermediate result
+    # that never reach the final result are the UIR of Section 1.1
+    used = {(int(a), int(b)) for a, b in j.rowids[:, :2].tolist()}
+    uir = j.intermediate[1] - len(used)
+    expect = [int(f[3]) for f in facts if f[0] == "uir"][0]
+    assert uir == expect == 15
+    T1 = q.relations[0]
+    assert int((T1.keys[0] == 3).sum()) == 6
+    assert int((O.columns(q, j.rowids)[0] == 3).sum()) == 32
+
+
+def test_figure1_generator_values():
+    """Messages and root weights of the running example (Section 3.3):
+    fac = 1 at the leaf, phi(C) from T3, phi(B) from T2 and T3, the root
+    marginal p(A) = (a3, 32), and the multiplicity of (b4, c3) = 16."""
+    q, *_ = golden_fig.load()
+    c = O.count(q, rows=True)
+    T2, T3 = q.relations[1], q.relations[2]
+    assert (c.up[2] == 1).all()                               # leaf rows
+    msg_c = Counter(int(x) for x in T3.keys[0])
+    assert dict(msg_c) == {1: 4, 2: 4, 3: 2, 4: 2}
+    msg_b = Counter()
+    for r in range(T2.n_rows):
+        msg_b[int(T2.keys[0][r])] += int(c.up[1][r])
+    assert {b: v for b, v in msg_b.items() if v} == {2: 12, 3: 4, 4: 6}
+    gm = O.group_mult_from_counts(q, c)
+    t1 = {tuple(k): int(m) for k, m in zip(gm[0][0].tolist(), gm[0][1])}
+    assert t1[(3, 3)] == 8 and t1[(3, 4)] == 24 and t1[(0, 0)] == 0
+    t2 = {tuple(k): int(m) for k, m in zip(gm[1][0].tolist(), gm[1][1])}
+    assert t2[(4, 3)] == 16 and t2[(4, 4)] == 8 and t2[(3, 2)] == 8
+
+
+# ------------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("q", tiny_queries(), ids=lambda q: q.name)
+def test_oracle_matches_nested_loops(q):
+    pl = O.plan(q)
+    bf = canonical(q, brute_force(q), pl.V)
+    c = O.count(q, rows=True)
+    assert c.total == len(bf) and not c.overflow
+    if not bf:
+        return
+    j = O.join(q)
+    assert [tuple(t) for t in j.rowids.tolist()] == [tuple(t) for t in bf]
+    # materialised columns: V values, then payloads by row id
+    cols = O.columns(q, j.rowids)
+    for i, t in enumerate(bf[:50]):
+        assert [int(cols[v][i]) for v in range(len(pl.V))] == [value_of(q, t, a) for a in pl.V]
+        pc = len(pl.V)
+        for jj, R in enumerate(q.relations):
+            for p in R.payloads:
+                assert int(cols[pc][i]) == int(p[t[jj]])
+                pc += 1
+    # summary levels
+    lv = O.gfjs_levels(q, j.rowids)
+    ref = levels_by_definition(q, bf, pl.V)
+    for l in range(len(pl.V)):
+        assert [list(x) for x in zip(lv[l].value.tolist(), lv[l].freq.tolist(),
+                                     lv[l].offset.tolist())] == ref[l]
+    # per key-tuple multiplicities, two ways
+    gm_c = O.group_mult_from_counts(q, c)
+    gm_r = O.group_mult_from_rows(q, j.rowids)
+    for jj, R in enumerate(q.relations):
+        cnt = Counter(tuple(int(R.keys[ci][t[jj]]) for ci in range(len(R.keys))) for t in bf)
+        got = {tuple(k): int(m) for k, m in zip(gm_c[jj][0].tolist(), gm_c[jj][1])}
+        assert {k: v for k, v in got.items() if v} == dict(cnt)
+        assert (gm_c[jj][1] == gm_r[jj][1]).all()
+        assert int(gm_c[jj][1].sum()) == c.total   # each relation sums to |Q|
+
+
+def test_cyclic_query_is_rejected():
+    a = np.array([0, 1], np.int32)
+    q = G.Query("triangle", [G.Relation("R", [0, 1], [a, a]),
+                             G.Relation("S", [1, 2], [a, a]),
+                             G.Relation("T", [2, 0], [a, a])])
+    with pytest.raises(O.NotAcyclic):
+        O.plan(q)
+
+
+def test_plan_of_branching_tree():
+    z = np.zeros(1, np.int32)
+    # R0(A,B) root; R1(B,C) under R0; R2(A,D) under R0; R3(C,E) under R1
+    q = G.Query("tree", [G.Relation("R0", [0, 1], [z, z]), G.Relation("R1", [1, 2], [z, z]),
+                         G.Relation("R2", [0, 3], [z, z]), G.Relation("R3", [2, 4], [z, z])])
+    pl = O.plan(q)
+    assert pl.parent == [-1, 0, 0, 1]
+    assert pl.preorder == [0, 1, 3, 2]
+    assert pl.V == [0, 1, 2, 4, 3]
+
+
+# ------------------------------------------------------------------ closed forms
+
+def _all_equal_star(sizes, value=7):
+    rels = [G.Relation(f"R{i}", [0], [np.full(n, value, np.int32)]) for i, n in enumerate(sizes)]
+    return G.Query("allequal", rels)
+
+
+def test_all_keys_equal_gives_product():
+    sizes = [3, 4, 5, 6]
+    c = O.count(_all_equal_star(sizes))
+    assert c.total == 3 * 4 * 5 * 6
+
+
+def test_empty_table_gives_zero():
+    q = G.chain3_uniform(rows=100, end_domain=10, mid_domain=5)
+    q.relations[1] = G.Relation("R2", [1, 2], [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int32)])
+    assert O.count(q).total == 0
+    q0 = G.chain3_uniform(rows=100, end_domain=10, mid_domain=5)
+    q0.relations[0] = G.Relation("R1", [0, 1], [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int32)])
+    assert O.count(q0).total == 0
+
+
+def test_primary_key_foreign_key_chain_counts_surviving_rows():
+    rng = np.random.default_rng(5)
+    fact_fk = rng.integers(0, 200, size=5000, dtype=np.int32)
+    dim_pk = np.arange(0, 200, 2, dtype=np.int32)          # every other key exists
+    rng.shuffle(dim_pk)
+    q = G.Query("pkfk", [G.Relation("F", [0], [fact_fk]), G.Relation("D", [0], [dim_pk])])
+    assert O.count(q).total == int((fact_fk % 2 == 0).sum())
+
+
+def test_uniform_chain_expected_size():
+    # E|Q| = n^3 / (|dom B| |dom C|) = 10^12 / 10^6 for the uniform 3-chain
+    c = O.count(G.chain3_uniform())
+    assert abs(c.total - 10**6) < 0.05 * 10**6
+
+
+def test_agm_bound_holds_on_chains():
+    # chain R1(A,B) R2(B,C) R3(C,D) over sets (the bound of Eq. 1 is for
+    # relations without duplicate rows): lambda = (1, 0, 1) covers every
+    # attribute, so |Q| <= |R1| |R3|
+    for seed in range(20):
+        q = G.chain_query("c", [30, 40, 50], [6, 3, 3, 6], [0.5] * 4, None, seed)
+        for i, R in enumerate(q.relations):
+            u = np.unique(np.stack(R.keys, axis=1), axis=0)
+            q.relations[i] = G.Relation(R.name, R.attrs, [u[:, 0].copy(), u[:, 1].copy()])
+        n1, n3 = q.relations[0].n_rows, q.relations[2].n_rows
+        assert O.count(q).total <= n1 * n3
+
+
+# ------------------------------------------------------------------ 2^64 boundary
+
+def test_largest_exact_count_is_two_pow_64_minus_2():
+    sizes = [2, 7, 7, 73, 127, 337, 92737, 649657]        # product = 2^64 - 2
+    c = O.count(_all_equal_star(sizes))
+    assert c.total == (1 << 64) - 2 and not c.overflow
+
+
+def test_two_pow_64_minus_1_reports_overflow():
+    sizes = [3, 5, 17, 257, 641, 65537, 6700417]           # product = 2^64 - 1
+    c = O.count(_all_equal_star(sizes))
+    assert c.overflow and c.total == CAP
+
+
+def test_beyond_two_pow_64_reports_overflow():
+    c = O.count(_all_equal_star([256] * 9))               # 2^72
+    assert c.overflow and c.total == CAP
+
+
+def test_dead_branch_never_reports_overflow():
+    # R0(A) holds only A=1; the subtree under A=2 has 256^8 = 2^64 ways
+    rels = [G.Relation("R0", [0], [np.array([1, 1, 1], np.int32)])]
+    rels.append(G.Relation("R1", [0, 1], [np.full(256, 2, np.int32), np.zeros(256, np.int32)]))
+    for i in range(2, 9):
+        rels.append(G.Relation(f"R{i}", [1], [np.zeros(256, np.int32)]))
+    rels.append(G.Relation("R9", [0], [np.array([1, 2], np.int32)]))
+    q = G.Query("dead", rels)
+    c = O.count(q, rows=True)
+    assert c.total == 0 and not c.overflow
+    assert all(int(m.max(initial=0)) == 0 for m in c.mult)
+
+
+def test_aligned_zipf_chain_overflows():
+    # heavy hitters that line up across tables (key = rank): the 5-chain's
+    # size is far above 2^64 (Section 8 overflow case), at reduced scale
+    q = G.chain5_zipf(rows=10**6, domain=10**5, aligned=True)
+    c = O.count(q)
+    assert c.overflow
+    # the same tables with per-column permutations stay exact
+    q2 = G.chain5_zipf(rows=10**5, domain=10**5)
+    c2 = O.count(q2)
+    assert not c2.overflow and 0 < c2.total < CAP
