@@ -1,0 +1,362 @@
+"""Benchmark of the Graphical Join hot path on GB300.
+
+One step = the whole path over one synthetic instance of the workload:
+factor construction of every relation, the summary (upward and downward
+sum-product passes, offsets), and desummarisation of every result row into
+device columns, chunk by chunk.  Inputs are resident in HBM before the timed
+region (they are larger than L2, so no flush is needed between steps).
+
+Default workload: 5-table chain R_i(K_{i-1}, K_i), 10^7 rows per table,
+int32 keys Zipf(s=1.1) over a domain of 10^6 (independently permuted per
+table and column), one int64 payload per table; desummarised in 2^28-row
+chunks.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "result tuples materialised/s"
+UNIT = "tuples/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gj", choices=["gj", "reference"])
+    p.add_argument("--rows", type=int, default=10**7)
+    p.add_argument("--domain", type=int, default=10**6)
+    p.add_argument("--zipf", type=float, default=1.1)
+    p.add_argument("--chunk-log2", type=int, default=28)
+    p.add_argument("--e2e-chunk-log2", type=int, default=24)
+    p.add_argument("--e2e-steps", type=int, default=1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-rows", type=int, default=20000)
+    return p.parse_args()
+
+
+def workload_name(a):
+    return (f"chain5_zipf: 5-table chain R_i(K_i-1,K_i), {a.rows} rows/table, int32 keys "
+            f"Zipf({a.zipf}) over [0,{a.domain}), int64 payload/table, "
+            f"desummarised in 2^{a.chunk_log2}-row chunks")
+
+
+def make_query(a, rank):
+    from paper_2206_10435_gb300 import datagen as G
+    return G.chain5_zipf(seed=G.SEED_BASE + 1 + 1000 * rank, rows=a.rows, domain=a.domain,
+                         s=a.zipf)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(a, q_full, sample_rows):
+    """The oracle, as it stands, on a bounded sample: the same tables with
+    the root restricted to its first `sample_rows` rows (a sub-join of the
+    workload); cascade of hash joins + canonical sort + column materialisation
+    on one host core."""
+    from oracle import oracle as O
+    from paper_2206_10435_gb300 import datagen as G
+    O.build()
+    R1 = q_full.relations[0]
+    sub = G.Relation(R1.name, R1.attrs, [k[:sample_rows].copy() for k in R1.keys],
+                     [p[:sample_rows].copy() for p in R1.payloads])
+    qs = G.Query("sample", [sub] + q_full.relations[1:], q_full.attr_names)
+    t0 = time.perf_counter()
+    j = O.join(qs, max_tuples=400_000_000)
+    cols = O.columns(qs, j.rowids)
+    dt = time.perf_counter() - t0
+    n = int(j.rowids.shape[0])
+    del cols
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"root relation cut to its first {sample_rows} of {R1.n_rows} rows, "
+                       f"other tables whole: {n} result tuples materialised in {dt:.2f} s "
+                       f"(hash-join cascade + canonical sort + columns)"),
+            "seconds": dt, "tuples": n}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    q = make_query(a, 0)
+    for _ in range(a.warmup):
+        cpu_baseline(a, q, a.cpu_sample_rows // 4)
+    vals, secs, tuples = [], 0.0, 0
+    for _ in range(a.steps):
+        r = cpu_baseline(a, q, a.cpu_sample_rows // 4)
+        secs += r["seconds"]
+        tuples += r["tuples"]
+    value = tuples / secs
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": 1000 * secs / a.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": workload_name(a), "inputs": "larger than L2"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"root cut to first {a.cpu_sample_rows // 4} rows per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        return run_reference(a, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2206_10435_gb300 import gj
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    q = make_query(a, rank)
+    rels = []
+    for R in q.relations:
+        rels.append(([torch.from_numpy(k).to(dev) for k in R.keys],
+                     [torch.from_numpy(p).to(dev) for p in R.payloads], R.attrs))
+    in_bytes = sum(sum(t.numel() * t.element_size() for t in ks + ps) for ks, ps, _ in rels)
+    stream = torch.cuda.Stream(dev)
+    ctx = gj.Context(local, stream)
+    CH = 1 << a.chunk_log2
+    out_bufs = None
+    phase = {"build_ms": 0.0, "summary_ms": 0.0, "desum_ms": 0.0}
+
+    def step(record=False):
+        nonlocal out_bufs
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+        if record:
+            ev[0].record(stream)
+        ids = [ctx.load_relation(ks, attrs, ps) for ks, ps, attrs in rels]
+        qq = ctx.query(ids)                       # factor construction
+        if record:
+            ev[1].record(stream)
+        total = qq.summarize()                    # upward + downward passes
+        if record:
+            ev[2].record(stream)
+        if out_bufs is None:
+            out_bufs = qq.alloc_columns(min(CH, total))
+        for r0 in range(0, total, CH):
+            qq.desummarize(r0, CH, out=out_bufs)
+        if record:
+            ev[3].record(stream)
+        qq.close()
+        for i in ids:
+            ctx.release_relation(i)
+        return total, ev
+
+    with torch.cuda.stream(stream):
+        total = 0
+        for _ in range(a.warmup):
+            total, _ = step()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        evs = []
+        for _ in range(a.steps):
+            total, ev = step(record=True)
+            evs.append(ev)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        prof = ctx.profile(False)
+        elapsed_ms = t_start.elapsed_time(t_end)
+        for ev in evs:
+            phase["build_ms"] += ev[0].elapsed_time(ev[1]) / a.steps
+            phase["summary_ms"] += ev[1].elapsed_time(ev[2]) / a.steps
+            phase["desum_ms"] += ev[2].elapsed_time(ev[3]) / a.steps
+    rows_local = total * a.steps
+    t_max = elapsed_ms
+    rows_all = rows_local
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        r = torch.tensor([rows_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(r)
+        rows_all = int(r.item())
+    value = rows_all / (t_max / 1000.0)
+
+    # end to end through the C ABI with host buffers: H2D of the relations
+    # from pinned memory, the whole path, D2H of every result chunk
+    e2e = None
+    if not a.no_e2e:
+        e2e = run_e2e(a, q, ctx, stream, dev, total, dist)
+
+    peak, peak_kind = measured_peaks()
+    achieved = (prof["emit_bytes"] / (prof["emit_ms"] * 1e6)) if prof["emit_ms"] else None
+    roofline = {"bound": "hbm", "kernel": "k_emit (desummarise emit)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
+                "bytes_per_launch": prof["emit_bytes"] / max(prof["emit_launches"], 1),
+                "avg_launch_ms": prof["emit_ms"] / max(prof["emit_launches"], 1)}
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(a, q, a.cpu_sample_rows)
+        cpu.pop("seconds")
+        cpu.pop("tuples")
+    if rank == 0:
+        row_bytes = sum(4 for _ in range(6)) + 8 * 5
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "int64", "data": "synthetic",
+               "config": {"workload": workload_name(a), "join_size": total,
+                          "result_row_bytes": row_bytes, "input_bytes": in_bytes,
+                          "l2": "inputs larger than L2 (no flush)",
+                          "parallelism": f"{world} independent instances (one per GPU)"},
+               "summary_build_ms": phase["build_ms"] + phase["summary_ms"],
+               "phases_ms": phase,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": int(prof["launches"]), "clocks": clk}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(a, q, ctx, stream, dev, total, dist):
+    import torch
+    from paper_2206_10435_gb300 import gj
+    host = []
+    h2d = 0
+    for R in q.relations:
+        ks = [torch.from_numpy(k).pin_memory() for k in R.keys]
+        ps = [torch.from_numpy(p).pin_memory() for p in R.payloads]
+        h2d += sum(t.numel() * t.element_size() for t in ks + ps)
+        host.append((ks, ps, R.attrs))
+    CH = 1 << a.e2e_chunk_log2
+    d2h = 0
+    with torch.cuda.stream(stream):
+        ids0 = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
+        qq0 = ctx.query(ids0)
+        qq0.summarize()
+        dbuf = qq0.alloc_columns(CH)
+        hbuf = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dbuf]
+        qq0.close()
+        for i in ids0:
+            ctx.release_relation(i)
+        row_bytes = sum(t.element_size() for t in dbuf)
+
+        def one():
+            ids = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
+            qq = ctx.query(ids)
+            tot = qq.summarize()
+            for r0 in range(0, tot, CH):
+                cols = qq.desummarize(r0, CH, out=dbuf)
+                m = cols[0].shape[0]
+                for h, d in zip(hbuf, cols):
+                    h[:m].copy_(d, non_blocking=True)
+            stream.synchronize()
+            qq.close()
+            for i in ids:
+                ctx.release_relation(i)
+            return tot
+
+        one()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            tot = one()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    d2h = tot * row_bytes
+    return {"value": tot * a.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
+            "chunk_rows": CH, "note": "relations H2D from pinned host memory, every result "
+                                      "chunk D2H into pinned host memory, inside the timed region"}
+
+
+if __name__ == "__main__":
+    main()

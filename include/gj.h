@@ -1,0 +1,222 @@
+/*
+ * gj.h -- C ABI of the GB300 Graphical Join library (libgj.so).
+ *
+ * Graphical Join (Shanghooshabad & Triantafillou, arXiv 2206.10435) computes
+ * an acyclic n-way equi-join in three steps, all of them CUDA kernels here:
+ *
+ *   1. factor construction (Section 3.2): every relation is scanned once and
+ *      grouped by its join-key tuple, giving the exact frequency table
+ *      ("potential") of the relation;
+ *   2. summarisation (Section 3.3, Algorithm 2; Section 3.5, Algorithms 3-4):
+ *      a sum-product pass over the join tree in the counting semiring,
+ *      leaves to root and back, giving the join size |Q| (the partition
+ *      function Z of Eq. 3), per key-tuple result multiplicities and the
+ *      offsets that place every distinct key path in the sorted result;
+ *   3. desummarisation (Section 3.6): any window of rows of the sorted join
+ *      result is expanded from that summary into caller-owned columns.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named "dev" or documented as device pointers must be CUDA
+ *   device memory of the context's device (torch tensors qualify); all other
+ *   pointers are host memory.
+ * - All work is enqueued on the context's stream.  Calls that return a host
+ *   value computed on the device (gj_summarize, gj_query_sizes, gj_level,
+ *   gj_desummarize's *n_out) synchronise that stream before returning.
+ * - Errors are returned, never raised: no call aborts the process and no
+ *   kernel traps.  Device-side waits are bounded and report GJ_ERR_TIMEOUT.
+ * - Counts are exact unsigned 64-bit integers.  UINT64_MAX is reserved as
+ *   the saturation marker: a join whose size is 2^64 - 1 or more reports
+ *   GJ_ERR_OVERFLOW.  A dead branch (a zero count) never overflows.
+ * - Limits: a relation holds at most 2^31 - 1 rows and at most 8 key
+ *   columns; a query joins at most 16 relations.  Key values are int32 and
+ *   ordered as signed integers.
+ */
+#ifndef GJ_H
+#define GJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GJ_OK = 0,
+    GJ_ERR_INVALID = 1,      /* bad argument, unknown id, size beyond a limit */
+    GJ_ERR_NOT_ACYCLIC = 2,  /* relation order does not give a join tree */
+    GJ_ERR_OOM = 3,          /* device allocation failed */
+    GJ_ERR_OVERFLOW = 4,     /* |Q| >= 2^64 - 1 */
+    GJ_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    GJ_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    GJ_ERR_STATE = 7,        /* call out of order (e.g. desummarise before summarise) */
+    GJ_ERR_CAPACITY = 8      /* caller's output buffer too small; *n_out holds the need */
+} gj_status;
+
+typedef struct gj_ctx gj_ctx;
+typedef struct gj_query gj_query;
+
+/* Relation columns live on the device unless GJ_REL_HOST is set. */
+#define GJ_REL_BORROW 0u     /* keep the caller's device pointers; caller keeps them alive */
+#define GJ_REL_COPY 1u       /* copy the columns into library-owned device memory */
+#define GJ_REL_HOST 2u       /* columns are host pointers; implies a copy (H2D) */
+
+/*
+ * One relation (a table of the join, Section 1.1).  Key columns are the join
+ * attributes: two relations join on every attribute id they share.  Payload
+ * columns are the non-join attributes, conditionally independent of each
+ * other given the join attributes (Section 3.2), and are carried by row id.
+ */
+typedef struct {
+    int64_t n_rows;
+    int32_t n_keys;                    /* 1..8 */
+    const int32_t *key_attr;           /* [n_keys] attribute id of every key column */
+    const int32_t *const *key_cols;    /* [n_keys] -> int32[n_rows] */
+    int32_t n_payloads;                /* 0..8 */
+    const int32_t *payload_width;      /* [n_payloads] bytes per value: 4 or 8 */
+    const void *const *payload_cols;   /* [n_payloads] -> width * n_rows bytes */
+    uint32_t flags;                    /* GJ_REL_* */
+} gj_relation_desc;
+
+/* Result-shape description of a query (filled by gj_query_sizes). */
+typedef struct {
+    int32_t n_rel;
+    int32_t n_vars;                    /* |V|: key columns of the result */
+    int32_t var_attr[64];              /* attribute id of result key column i */
+    int32_t n_cols;                    /* n_vars + all payload columns */
+    int32_t col_width[64];             /* bytes per value of result column i */
+    int32_t parent[16];                /* join tree: parent relation, -1 for the root */
+    int64_t n_groups[16];              /* distinct key tuples per relation */
+} gj_query_sizes_t;
+
+/* Counters of gj_profile. */
+typedef struct {
+    uint64_t launches;       /* kernels the context launched since the last read */
+    uint64_t emit_launches;  /* launches of the desummarise emit kernel while profiling */
+    double emit_ms;          /* their summed device time, from CUDA events on the stream */
+    uint64_t emit_rows;      /* result rows they wrote */
+    uint64_t emit_bytes;     /* bytes of result columns they wrote */
+} gj_profile_t;
+
+/* Library version and status text. */
+const char *gj_status_str(gj_status s);
+int32_t gj_version(void);
+
+/*
+ * Creates a context on CUDA device `device` that enqueues its work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * The context owns relations, factors and queries; gj_destroy frees them.
+ */
+gj_status gj_create(gj_ctx **out, int32_t device, void *cuda_stream);
+void gj_destroy(gj_ctx *ctx);
+gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
+
+/*
+ * Profiling (no counterpart in the paper, which reports wall-clock times
+ * only).  With out != NULL: synchronises the stream, writes the counters
+ * accumulated since the previous read and resets them.  Then turns device
+ * timing of the emit kernel on (enable != 0) or off.
+ */
+gj_status gj_profile(gj_ctx *ctx, int32_t enable, gj_profile_t *out);
+
+/*
+ * Registers a relation (Section 1.1: the tables T_1..T_n to be joined).
+ * Column pointers are device pointers (GJ_REL_BORROW, GJ_REL_COPY) or host
+ * pointers (GJ_REL_HOST).  Borrowed columns must outlive the relation.
+ * Returns its id in *rel_id.
+ */
+gj_status gj_load_relation(gj_ctx *ctx, const gj_relation_desc *desc, int32_t *rel_id);
+gj_status gj_release_relation(gj_ctx *ctx, int32_t rel_id);
+
+/*
+ * Factor construction (Section 3.2, "quantitative learning"): groups the
+ * relation's rows by their key tuple, ordered by the columns in `col_order`
+ * (a permutation of 0..n_keys-1, most significant first; NULL = declared
+ * order), rows of a group in increasing row id.  The result is the exact
+ * frequency table of the relation: distinct key tuples with their counts.
+ * Idempotent and cached per column order; factors may be built ahead of any
+ * query and reused by many (Section 3.2, last paragraph; Section 4.1).
+ */
+gj_status gj_build_factors(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order);
+
+/*
+ * Exports a built factor: *n_groups, and, for non-NULL device outputs,
+ * perm (uint32[n_rows], row ids in group order), gstart (uint32[n_groups+1],
+ * first position of every group in perm) and gkey (int32[n_keys*n_groups],
+ * key column c of group g at gkey[c*n_groups + g]).  Call once with NULL
+ * outputs to learn n_groups.
+ */
+gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order,
+                           int64_t *n_groups, uint32_t *perm_dev, uint32_t *gstart_dev,
+                           int32_t *gkey_dev);
+
+/*
+ * Plans a query over relations rel_ids[0..n_rel-1] (rel_ids[0] is the root).
+ * Relation j > 0 hangs under the first earlier relation that holds every
+ * attribute j shares with relations 0..j-1; if there is none the order does
+ * not give a join tree (GJ_ERR_NOT_ACYCLIC); if j shares nothing the query
+ * is rejected (GJ_ERR_INVALID).  The result's key columns V are a preorder
+ * walk of that tree, every relation adding the attributes its parent lacks
+ * in declared column order; payload columns follow, relation by relation.
+ * Rows of the result are ordered by V (signed int32, ascending), ties broken
+ * by the original row ids r_1..r_k (Def. 1 sorts the result by all columns).
+ * Builds any factor it needs.
+ */
+gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out);
+void gj_query_destroy(gj_query *q);
+gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out);
+
+/*
+ * Summarisation: the upward sum-product pass of Algorithm 2 over the join
+ * tree in the counting semiring (Eqs. 4-10: product of a relation's
+ * frequencies with its children's messages, summed out over the separator),
+ * the root marginal whose sum is the join size (Section 3.3), and the
+ * downward pass that gives every distinct key tuple of every relation its
+ * result multiplicity and every key path its offset in the sorted result
+ * (the bucket products of Algorithm 4).  Writes |Q| to *total (UINT64_MAX
+ * when GJ_ERR_OVERFLOW).  Synchronises the stream.
+ */
+gj_status gj_summarize(gj_query *q, uint64_t *total);
+
+/*
+ * Per-group summary of relation position `rel` (0..n_rel-1) of the query,
+ * into device arrays of n_groups entries each (any may be NULL):
+ *   w:     result rows per (key tuple, fixed ancestors) = count x product of
+ *          the children's messages (the bucket * fac of Section 3.3)
+ *   mult:  number of result tuples that use the key tuple (its marginal
+ *          over the join result, Section 1.2 "Why PGMs")
+ *   off:   for the root, the first result row of the key tuple; for other
+ *          relations, the exclusive prefix of w within its separator segment
+ * Group order is the factor's (separator columns first).
+ */
+gj_status gj_summary_groups(gj_query *q, int32_t rel, uint64_t *w_dev, uint64_t *mult_dev,
+                            uint64_t *off_dev);
+
+/*
+ * GFJS column `level` (0..n_vars-1; Def. 1, Figure 2): the runs of the
+ * sorted result over distinct prefixes (v_0..v_level), one run per prefix
+ * (Algorithm 4 emits one entry per prefix), restricted to runs that START
+ * in result rows [row0, row0 + n_rows).  Writes value (int32), freq and
+ * offset (uint64) of each run into device arrays of capacity `cap`; *n_out
+ * receives the number of runs (GJ_ERR_CAPACITY if above cap).
+ */
+gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
+                   int32_t *value_dev, uint64_t *freq_dev, uint64_t *offset_dev,
+                   uint64_t cap, uint64_t *n_out);
+
+/*
+ * Desummarisation (Section 3.6): writes result rows [row0, row0 + n_rows)
+ * (clipped to |Q|) into caller-owned device columns out_cols[0..n_cols-1]
+ * (layout from gj_query_sizes: the V key columns as int32, then payloads).
+ * If rowid_cols is non-NULL, rowid_cols[j] (device uint32[n_rows], may be
+ * NULL per relation) receives the row id r_j of every result row.
+ * *n_out receives the number of rows written.  Requires gj_summarize.
+ */
+gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
+                         void *const *out_cols, uint32_t *const *rowid_cols, uint64_t *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H */

@@ -1,0 +1,266 @@
+// gj_factor.cu -- factor construction (Section 3.2, quantitative learning).
+//
+// A relation's potential is its exact frequency table: the distinct key
+// tuples with their counts.  Here it is built by sorting the rows by their
+// key tuple and cutting the sorted order into groups:
+//
+//   1. per key column, min and max (one read of every column);
+//   2. each column becomes an unsigned field of ceil(log2(max-min+1)) bits;
+//      fields are packed into 64-bit words, most significant column first,
+//      and the words are sorted least significant first with the stable
+//      radix sort (one word suffices unless the fields exceed 64 bits);
+//   3. group heads are the rows whose packed key differs from the previous
+//      row's; an exclusive scan numbers the groups;
+//   4. each group records its first position and its key values; payload
+//      columns are gathered into group order.
+//
+// Sorted order is also the order the desummariser walks: groups sharing a
+// separator value are contiguous (the separator columns lead the order) and
+// inside a group rows keep increasing row id.
+#include <algorithm>
+
+#include "gj_state.cuh"
+
+namespace gj {
+namespace {
+
+constexpr int FT = 256;
+
+struct ColSet {
+    int ncol;
+    const int32_t *col[MAX_KEYS];
+};
+
+__global__ void k_minmax_init(int nk, int32_t *mm) {
+    int c = threadIdx.x;
+    if (c < nk) { mm[2 * c] = INT32_MAX; mm[2 * c + 1] = INT32_MIN; }
+}
+
+__global__ void k_minmax(ColSet cs, int64_t n, int32_t *mm) {
+    int c = blockIdx.y;
+    const int32_t *col = cs.col[c];
+    int32_t lo = INT32_MAX, hi = INT32_MIN;
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        int32_t v = col[i];
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    for (int d = 16; d; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[2 * c], lo);
+        atomicMax(&mm[2 * c + 1], hi);
+    }
+}
+
+struct PackSpec {
+    int ncol;
+    const int32_t *col[MAX_KEYS];
+    int32_t mn[MAX_KEYS];
+    int shift[MAX_KEYS];
+};
+
+// keys[i] = packed fields of row (rows ? rows[i] : i); vals[i] = that row
+__global__ void k_pack(PackSpec ps, const uint32_t *__restrict__ rows, int64_t n,
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        uint32_t r = rows ? rows[i] : (uint32_t)i;
+        uint64_t k = 0;
+#pragma unroll
+        for (int c = 0; c < MAX_KEYS; c++) {
+            if (c < ps.ncol && ps.shift[c] < 64)
+                k |= (uint64_t)((uint32_t)ps.col[c][r] - (uint32_t)ps.mn[c]) << ps.shift[c];
+        }
+        keys[i] = k;
+        vals[i] = r;
+    }
+}
+
+// head[i] = i == 0 || key tuple of perm[i] != key tuple of perm[i-1]
+__global__ void k_heads_packed(const uint64_t *__restrict__ keys, int64_t n, uint8_t *head) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        head[i] = (i == 0) || keys[i] != keys[i - 1];
+}
+
+__global__ void k_heads_gather(ColSet cs, const uint32_t *__restrict__ perm, int64_t n,
+                               uint8_t *head) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        uint8_t h = (i == 0);
+        if (!h) {
+            uint32_t a = perm[i], b = perm[i - 1];
+            for (int c = 0; c < cs.ncol; c++)
+                if (cs.col[c][a] != cs.col[c][b]) { h = 1; break; }
+        }
+        head[i] = h;
+    }
+}
+
+__global__ void k_group_compact(ColSet cs, const uint32_t *__restrict__ perm,
+                                const uint8_t *__restrict__ head, const uint32_t *__restrict__ gid,
+                                int64_t n, int64_t G, uint32_t *gstart, int32_t *gkey) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        if (!head[i]) continue;
+        uint32_t g = gid[i];
+        gstart[g] = (uint32_t)i;
+        uint32_t r = perm[i];
+        for (int c = 0; c < cs.ncol; c++) gkey[(int64_t)c * G + g] = cs.col[c][r];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
+}
+
+template <class T>
+__global__ void k_gather(const T *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
+                         T *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        dst[i] = src[perm[i]];
+}
+
+inline int grid_for(Ctx &c, int64_t n) {
+    int64_t b = ceil_div(n, FT);
+    int64_t cap = (int64_t)c.num_sms * 16;
+    return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+inline int bits_of(uint32_t range) { return range == 0 ? 0 : 32 - __builtin_clz(range); }
+
+}  // namespace
+
+cudaError_t relation_minmax(Ctx &c, Relation &R) {
+    if (R.have_minmax) return cudaSuccess;
+    R.kmin.assign(R.nk, 0);
+    R.kmax.assign(R.nk, 0);
+    if (R.n > 0) {
+        int32_t *mm = nullptr;
+        GJ_CUDA_TRY(dalloc(c, &mm, 2 * R.nk));
+        ColSet cs{};
+        cs.ncol = R.nk;
+        for (int i = 0; i < R.nk; i++) cs.col[i] = R.key[i];
+        k_minmax_init<<<1, 32, 0, c.stream>>>(R.nk, mm); c.launches++;
+        dim3 grid((unsigned)std::max(1, grid_for(c, R.n) / std::max(1, R.nk)), R.nk);
+        k_minmax<<<grid, FT, 0, c.stream>>>(cs, R.n, mm); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        // device->host readbacks go through the pinned buffer, then sync
+        int32_t *h = (int32_t *)c.pinned;
+        GJ_CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(int32_t) * 2 * R.nk, cudaMemcpyDeviceToHost, c.stream));
+        GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        for (int i = 0; i < R.nk; i++) { R.kmin[i] = h[2 * i]; R.kmax[i] = h[2 * i + 1]; }
+        dfree(c, mm);
+    }
+    R.have_minmax = true;
+    return cudaSuccess;
+}
+
+void factor_free(Ctx &c, Factor &F) {
+    dfree(c, F.perm);
+    dfree(c, F.gstart);
+    dfree(c, F.gkey);
+    for (void *&p : F.pay) dfree(c, p);
+    F.pay.clear();
+}
+
+cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Factor &F) {
+    F.order = order;
+    F.n = R.n;
+    const int64_t n = R.n;
+    GJ_CUDA_TRY(relation_minmax(c, R));
+    GJ_CUDA_TRY(dalloc(c, &F.perm, n));
+    if (n == 0) {
+        F.G = 0;
+        GJ_CUDA_TRY(dalloc(c, &F.gstart, 1));
+        GJ_CUDA_TRY(cudaMemsetAsync(F.gstart, 0, sizeof(uint32_t), c.stream));
+        GJ_CUDA_TRY(dalloc(c, &F.gkey, 1));
+        for (int p = 0; p < R.np; p++) {
+            void *d = nullptr;
+            GJ_CUDA_TRY(cudaMallocAsync(&d, 16, c.stream));
+            F.pay.push_back(d);
+        }
+        return cudaSuccess;
+    }
+    // field widths, least significant column last in `order`
+    std::vector<int> bits(R.nk);
+    for (int i = 0; i < R.nk; i++)
+        bits[i] = bits_of((uint32_t)((int64_t)R.kmax[i] - (int64_t)R.kmin[i]));
+    // cut the order into words of <= 64 bits, starting from the least
+    // significant column
+    std::vector<std::vector<int>> words;
+    {
+        std::vector<int> cur;
+        int used = 0;
+        for (int i = (int)order.size() - 1; i >= 0; i--) {
+            int col = order[i];
+            if (used + bits[col] > 64 && !cur.empty()) {
+                words.push_back(cur);
+                cur.clear();
+                used = 0;
+            }
+            cur.push_back(col);
+            used += bits[col];
+        }
+        if (!cur.empty()) words.push_back(cur);
+    }
+    uint64_t *keys = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &keys, n));
+    bool first = true;
+    for (auto &wcols : words) {   // least significant word first
+        PackSpec ps{};
+        ps.ncol = (int)wcols.size();
+        int shift = 0;
+        for (int i = 0; i < ps.ncol; i++) {   // wcols[0] is the least significant
+            int col = wcols[i];
+            ps.col[i] = R.key[col];
+            ps.mn[i] = R.kmin[col];
+            ps.shift[i] = shift;
+            shift += bits[col];
+        }
+        k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, first ? nullptr : F.perm, n, keys, F.perm); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        GJ_CUDA_TRY(radix_sort_u64_u32(c, keys, F.perm, n, shift));
+        first = false;
+    }
+    uint8_t *head = nullptr;
+    uint32_t *gid = nullptr, *gcount = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &head, n));
+    GJ_CUDA_TRY(dalloc(c, &gid, n));
+    GJ_CUDA_TRY(dalloc(c, &gcount, 1));
+    ColSet all{};
+    all.ncol = R.nk;
+    for (int i = 0; i < R.nk; i++) all.col[i] = R.key[i];
+    if (words.size() == 1) {
+        k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(keys, n, head); c.launches++;
+    } else {
+        k_heads_gather<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, head); c.launches++;
+    }
+    GJ_CUDA_TRY(cudaGetLastError());
+    GJ_CUDA_TRY(scan_u32(c, nullptr, head, gid, n, gcount));
+    uint32_t *hg = (uint32_t *)c.pinned;
+    GJ_CUDA_TRY(cudaMemcpyAsync(hg, gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    F.G = hg[0];
+    GJ_CUDA_TRY(dalloc(c, &F.gstart, F.G + 1));
+    GJ_CUDA_TRY(dalloc(c, &F.gkey, (size_t)R.nk * F.G));
+    k_group_compact<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, head, gid, n, F.G, F.gstart,
+                                                         F.gkey); c.launches++;
+    GJ_CUDA_TRY(cudaGetLastError());
+    for (int p = 0; p < R.np; p++) {
+        void *d = nullptr;
+        GJ_CUDA_TRY(cudaMallocAsync(&d, (size_t)R.pw[p] * n, c.stream));
+        if (R.pw[p] == 8) {
+            k_gather<uint64_t><<<grid_for(c, n), FT, 0, c.stream>>>(
+                (const uint64_t *)R.pay[p], F.perm, n, (uint64_t *)d); c.launches++;
+        } else {
+            k_gather<uint32_t><<<grid_for(c, n), FT, 0, c.stream>>>(
+                (const uint32_t *)R.pay[p], F.perm, n, (uint32_t *)d); c.launches++;
+        }
+        GJ_CUDA_TRY(cudaGetLastError());
+        F.pay.push_back(d);
+    }
+    dfree(c, keys);
+    dfree(c, head);
+    dfree(c, gid);
+    dfree(c, gcount);
+    return cudaSuccess;
+}
+
+}  // namespace gj

@@ -1,0 +1,113 @@
+// gj_internal.cuh -- shared definitions of the CUDA path (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gj.h"
+
+namespace gj {
+
+// ------------------------------------------------------------------ semiring
+// Counting semiring over N with a saturation marker SAT = 2^64 - 1 that
+// stands for "2^64 - 1 or more".  0 annihilates SAT, so a dead branch of the
+// join tree stays 0 however large the counts beneath it.
+
+constexpr uint64_t SAT = ~0ull;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+__host__ __device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+    uint64_t s = a + b;
+    return (s < a || s == SAT) ? SAT : s;
+}
+
+__device__ __forceinline__ uint64_t sat_mul(uint64_t a, uint64_t b) {
+    if (a == 0 || b == 0) return 0;
+    uint64_t hi = __umul64hi(a, b);
+    uint64_t lo = a * b;
+    return (hi != 0 || lo == SAT) ? SAT : lo;
+}
+
+// ------------------------------------------------------------------ errors
+// Device-side error word: kernels OR these bits in instead of trapping.
+enum : uint32_t {
+    ERRF_TIMEOUT = 1u,   // a bounded spin-wait gave up
+    ERRF_BOUNDS = 2u,    // an index check failed
+    ERRF_OVERFLOW = 4u,  // a count that must be exact saturated
+};
+
+// Upper bound on polls of a lookback flag before a kernel gives up.
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ void raise_err(uint32_t *err, uint32_t bits) {
+    if (err) atomicOr(err, bits);
+}
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t *err = nullptr;          // device error word
+    uint64_t *pinned = nullptr;       // small pinned host buffer for readbacks
+    int num_sms = 0;
+    uint64_t launches = 0;            // kernels launched (profiling)
+    // device-time profile of the emit kernel (CUDA events on the stream)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free, ev_used;
+    uint64_t emit_launches = 0, emit_rows = 0, emit_bytes = 0;
+    cudaEvent_t event() {
+        cudaEvent_t e = nullptr;
+        if (!ev_free.empty()) { e = ev_free.back(); ev_free.pop_back(); }
+        else cudaEventCreate(&e);
+        ev_used.push_back(e);
+        return e;
+    }
+};
+
+// Stream-ordered device allocation on the context's stream.
+template <class T>
+inline cudaError_t dalloc(Ctx &c, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMallocAsync((void **)p, count * sizeof(T), c.stream);
+}
+template <class T>
+inline void dfree(Ctx &c, T *&p) {
+    if (p) cudaFreeAsync((void *)p, c.stream);
+    p = nullptr;
+}
+
+// ------------------------------------------------------------------ primitives
+// Exclusive prefix sums, single pass with decoupled lookback.  All of them
+// are stream-ordered; *total_dev (if non-NULL) receives the sum.
+
+// u32: out[i] = sum of in[0..i); in may be NULL with flags != NULL, in which
+// case the summed value of i is (flags[i] != 0).
+cudaError_t scan_u32(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
+                     int64_t n, uint32_t *total_dev);
+
+// saturating u64, optionally segmented: heads[i] != 0 starts a new segment
+// (the exclusive value there is 0).  seg_total[s] (if non-NULL) receives the
+// saturating sum of segment s, with seg_id[i] mapping element i to its
+// segment (needed only when seg_total is set); total_dev gets the sum of the
+// last segment (or of everything, unsegmented).
+cudaError_t scan_u64_sat(Ctx &c, const uint64_t *in, const uint8_t *heads, uint64_t *out,
+                         int64_t n, uint64_t *total_dev, uint64_t *seg_total,
+                         const uint32_t *seg_id);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits).
+// keys/vals are sorted in place (ping-pong through internal buffers).
+cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits);
+
+// ------------------------------------------------------------------ helpers
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+#define GJ_CUDA_TRY(expr)                        \
+    do {                                         \
+        cudaError_t _e = (expr);                 \
+        if (_e != cudaSuccess) return _e;        \
+    } while (0)
+
+}  // namespace gj

@@ -1,0 +1,240 @@
+// gj_sort.cu -- stable LSD radix sort of (uint64 key, uint32 value) pairs.
+//
+// Used by factor construction to order a relation's rows by their packed
+// join-key tuple (Section 3.2: the frequency table is the run-length form of
+// the sorted rows).  8-bit digits, one "onesweep" launch per digit:
+//
+//   * one upfront pass reads every key once and builds the 256-bin
+//     histogram of every digit in shared memory (warp-private bins, then
+//     global atomics); a tiny kernel turns them into bucket bases;
+//   * per digit, each CTA takes the next tile id from a global counter,
+//     ranks its 4096 keys with a warp-level multi-split (__match_any_sync
+//     peers, per-warp bins, no atomics), publishes its per-digit counts,
+//     finds each digit's global offset by decoupled lookback over the
+//     preceding tiles (bounded polls, ERRF_TIMEOUT on expiry), stages the
+//     tile in shared memory in digit order and scatters it so that
+//     consecutive threads write consecutive addresses of a bucket.
+//
+// Stable: ranks follow (tile, warp, item, lane) order, which is input order.
+#include <algorithm>
+
+#include "gj_internal.cuh"
+
+namespace gj {
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;       // 4096 keys
+constexpr int RS_RADIX = 256;
+constexpr int RS_MAX_PASSES = 8;
+constexpr uint64_t ST_AGG = 1ull << 62, ST_PREFIX = 2ull << 62, ST_MASK = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_digit_hist(const uint64_t *__restrict__ keys, int64_t n, int passes, uint32_t *hist) {
+    __shared__ uint32_t sh[RS_MAX_PASSES][RS_RADIX];
+    for (int i = threadIdx.x; i < RS_MAX_PASSES * RS_RADIX; i += RS_THREADS) (&sh[0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * RS_THREADS) {
+        uint64_t k = keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&sh[p][(k >> (8 * p)) & 0xff], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * RS_RADIX; i += RS_THREADS) {
+        uint32_t v = (&sh[0][0])[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// hist[p][d] -> exclusive bucket base per pass (one CTA per pass)
+__global__ void __launch_bounds__(RS_RADIX) k_hist_to_base(uint32_t *hist) {
+    __shared__ uint32_t s[RS_RADIX];
+    uint32_t *h = hist + blockIdx.x * RS_RADIX;
+    int d = threadIdx.x;
+    s[d] = h[d];
+    __syncthreads();
+    for (int off = 1; off < RS_RADIX; off <<= 1) {
+        uint32_t v = d >= off ? s[d - off] : 0u;
+        __syncthreads();
+        s[d] += v;
+        __syncthreads();
+    }
+    h[d] = s[d] - h[d];
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+           const uint32_t *__restrict__ bucket_base, uint32_t *tile_counter,
+           unsigned long long *status, uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_keys = (uint64_t *)smem;                              // RS_TILE
+    uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);                // RS_TILE
+    uint32_t *s_whist = s_vals + RS_TILE;                             // RS_WARPS*RS_RADIX
+    uint32_t *s_tile_off = s_whist + RS_WARPS * RS_RADIX;             // RS_RADIX
+    uint32_t *s_glob = s_tile_off + RS_RADIX;                         // RS_RADIX
+    uint32_t *s_misc = s_glob + RS_RADIX;                             // 8
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_misc[0] = atomicAdd(tile_counter, 1u);
+    for (int i = tid; i < RS_WARPS * RS_RADIX; i += RS_THREADS) s_whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_misc[0];
+    const int64_t base = (int64_t)tile * RS_TILE;
+
+    uint64_t k[RS_ITEMS];
+    uint32_t v[RS_ITEMS];
+    uint32_t rank[RS_ITEMS];
+    const int64_t wbase = base + warp * (RS_ITEMS * 32);
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int64_t idx = wbase + i * 32 + lane;
+        if (idx < n) { k[i] = kin[idx]; v[i] = vin[idx]; }
+        else { k[i] = 0; v[i] = 0; }
+    }
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t *wh = s_whist + warp * RS_RADIX;
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int64_t idx = wbase + i * 32 + lane;
+        bool valid = idx < n;
+        uint32_t d = valid ? (uint32_t)((k[i] >> shift) & 0xff) : 0x100u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            old = wh[d];
+            wh[d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[i] = old + __popc(peers & lt_mask);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per digit: tile count, and per-warp exclusive offsets
+    const int d = tid;   // RS_THREADS == RS_RADIX
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; w++) {
+        uint32_t c = s_whist[w * RS_RADIX + d];
+        s_whist[w * RS_RADIX + d] = cnt;
+        cnt += c;
+    }
+    // publish the tile's count of digit d, then look back for its prefix
+    unsigned long long *st = status + (size_t)tile * RS_RADIX;
+    if (tile == 0) {
+        atomicExch(&st[d], (unsigned long long)(ST_PREFIX | cnt));
+        s_glob[d] = bucket_base[d];
+    } else {
+        atomicExch(&st[d], (unsigned long long)(ST_AGG | cnt));
+        uint64_t excl = 0;
+        int64_t p = (int64_t)tile - 1;
+        while (p >= 0) {
+            unsigned long long s;
+            uint32_t spins = 0;
+            while (((s = *(volatile unsigned long long *)&status[(size_t)p * RS_RADIX + d]) >> 62) == 0) {
+                if (++spins > SPIN_LIMIT) { raise_err(err, ERRF_TIMEOUT); s = ST_PREFIX; break; }
+            }
+            excl += s & ST_MASK;
+            if (s & ST_PREFIX) break;
+            p--;
+        }
+        atomicExch(&st[d], (unsigned long long)(ST_PREFIX | (excl + cnt)));
+        s_glob[d] = bucket_base[d] + (uint32_t)excl;
+    }
+    // tile-local exclusive offsets over digits
+    s_tile_off[d] = cnt;
+    __syncthreads();
+    {
+        // 256-wide inclusive scan in shared memory (Hillis-Steele)
+        for (int off = 1; off < RS_RADIX; off <<= 1) {
+            uint32_t t = d >= off ? s_tile_off[d - off] : 0u;
+            __syncthreads();
+            s_tile_off[d] += t;
+            __syncthreads();
+        }
+        s_tile_off[d] -= cnt;
+    }
+    __syncthreads();
+    // stage in digit order
+#pragma unroll
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int64_t idx = wbase + i * 32 + lane;
+        if (idx < n) {
+            uint32_t dg = (uint32_t)((k[i] >> shift) & 0xff);
+            uint32_t pos = s_tile_off[dg] + s_whist[warp * RS_RADIX + dg] + rank[i];
+            s_keys[pos] = k[i];
+            s_vals[pos] = v[i];
+        }
+    }
+    __syncthreads();
+    const int64_t tile_n = (n - base) < RS_TILE ? (n - base) : RS_TILE;
+#pragma unroll 4
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int p = i * RS_THREADS + tid;
+        if (p < tile_n) {
+            uint64_t key = s_keys[p];
+            uint32_t dg = (uint32_t)((key >> shift) & 0xff);
+            uint32_t dest = s_glob[dg] + (uint32_t)(p - s_tile_off[dg]);
+            kout[dest] = key;
+            vout[dest] = s_vals[p];
+        }
+    }
+}
+
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 8 + (size_t)RS_TILE * 4 +
+                           (size_t)RS_WARPS * RS_RADIX * 4 + 2 * RS_RADIX * 4 + 8 * 4;
+
+}  // namespace
+
+cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    if (n > 0x7fffffffLL || bits > 64) return cudaErrorInvalidValue;
+    static bool attr_set = false;
+    if (!attr_set) {
+        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RS_SMEM));
+        attr_set = true;
+    }
+    const int passes = (bits + 7) / 8;
+    const int64_t tiles = ceil_div(n, RS_TILE);
+    uint64_t *k2 = nullptr;
+    uint32_t *v2 = nullptr, *hist = nullptr, *counters = nullptr;
+    unsigned long long *status = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &k2, n));
+    GJ_CUDA_TRY(dalloc(c, &v2, n));
+    GJ_CUDA_TRY(dalloc(c, &hist, RS_MAX_PASSES * RS_RADIX + passes));
+    GJ_CUDA_TRY(dalloc(c, &status, (size_t)tiles * RS_RADIX));
+    counters = hist + RS_MAX_PASSES * RS_RADIX;
+    GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + passes),
+                                c.stream));
+    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
+    if (hist_blocks < 1) hist_blocks = 1;
+    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
+    uint64_t *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    for (int p = 0; p < passes; p++) {
+        GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
+                                    c.stream));
+        k_onesweep<<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
+            ka, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        GJ_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c.stream));
+        GJ_CUDA_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c.stream));
+    }
+    dfree(c, k2);
+    dfree(c, v2);
+    dfree(c, hist);
+    dfree(c, status);
+    return cudaSuccess;
+}
+
+}  // namespace gj

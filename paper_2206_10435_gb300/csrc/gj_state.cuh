@@ -1,0 +1,98 @@
+// gj_state.cuh -- host-side state of contexts, relations, factors, queries.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "gj_internal.cuh"
+
+namespace gj {
+
+constexpr int MAX_KEYS = 8;
+constexpr int MAX_PAYLOADS = 8;
+constexpr int MAX_REL = 16;
+
+// Frequency table of one relation (Section 3.2), ordered by `order`
+// (column indices, most significant first).  Rows of a group are contiguous
+// in perm and in increasing row id.
+struct Factor {
+    std::vector<int> order;
+    int64_t n = 0, G = 0;
+    uint32_t *perm = nullptr;      // [n]
+    uint32_t *gstart = nullptr;    // [G+1]
+    int32_t *gkey = nullptr;       // [nk*G], declared column c at c*G
+    std::vector<void *> pay;       // payloads in perm order (width*n bytes)
+};
+
+struct Relation {
+    int64_t n = 0;
+    int nk = 0, np = 0;
+    std::vector<int32_t> attr;
+    std::vector<const int32_t *> key;
+    std::vector<int32_t> pw;
+    std::vector<const void *> pay;
+    std::vector<void *> owned;     // library-owned copies
+    bool have_minmax = false;
+    std::vector<int32_t> kmin, kmax;
+    std::map<std::vector<int>, std::unique_ptr<Factor>> factors;
+};
+
+struct CtxState {
+    Ctx c;
+    std::map<int32_t, std::unique_ptr<Relation>> rels;
+    int32_t next_id = 1;
+};
+
+// Per-relation state of a query: the relation's place in the join tree and
+// its part of the summary.
+struct QRel {
+    int rel_id = 0;
+    Relation *R = nullptr;
+    Factor *F = nullptr;
+    int parent = -1;                   // position in the query
+    std::vector<int> children;         // positions, increasing
+    std::vector<int> sep_cols;         // separator columns in this relation
+    std::vector<int> sep_cols_parent;  // matching columns in the parent
+    std::vector<int> new_cols;         // columns whose attribute the parent lacks
+    // segments over the separator (non-root)
+    int64_t S = 0;
+    uint32_t *seg_id = nullptr;        // [G]
+    uint32_t *seg_first = nullptr;     // [S+1]
+    // link to each child's segments: link[i][g] for children[i]
+    std::vector<uint32_t *> link;
+    // summary
+    uint64_t *w = nullptr;             // [G]
+    uint64_t *off = nullptr;           // [G] root: global offset; else rel_off
+    uint64_t *msg = nullptr;           // [S] (non-root)
+    uint64_t *down = nullptr;          // [S] (non-root)
+    uint64_t *mult = nullptr;          // [G]
+    // live (w > 0) groups, in group order
+    int64_t L = 0;
+    uint32_t *lgid = nullptr;          // [L]
+    uint64_t *loff = nullptr;          // [L]
+    uint64_t *lw = nullptr;            // [L]
+    uint32_t *lseg_first = nullptr;    // [S+1] (non-root)
+};
+
+struct QueryState {
+    CtxState *cs = nullptr;
+    int k = 0;
+    std::vector<QRel> r;
+    std::vector<int> pre;              // preorder of positions
+    std::vector<int> pos;              // position -> preorder index
+    std::vector<int> var_rel, var_col; // V
+    std::vector<int> col_rel, col_pay; // payload output columns
+    bool summarized = false;
+    bool overflow = false;
+    uint64_t total = 0;
+};
+
+}  // namespace gj
+
+struct gj_ctx {
+    gj::CtxState s;
+};
+struct gj_query {
+    gj::QueryState s;
+};

@@ -1,0 +1,37 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads
+without a GPU and exports every function include/gj.h declares."""
+import ctypes
+
+from paper_2206_10435_gb300 import build, gj
+
+
+def test_header_declares_the_boundary_calls():
+    names = gj.header_functions()
+    for required in ["gj_create", "gj_destroy", "gj_load_relation", "gj_build_factors",
+                     "gj_query_create", "gj_summarize", "gj_summary_groups", "gj_level",
+                     "gj_desummarize", "gj_query_destroy", "gj_status_str"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    build.build()
+    L = ctypes.CDLL(build.LIB)
+    missing = [n for n in gj.header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu():
+    L = gj.lib()
+    assert L.gj_version() >= 1
+    for s in range(9):
+        assert L.gj_status_str(s)
+    assert L.gj_status_str(gj.GJ_ERR_OVERFLOW) == b"join size reaches 2^64 - 1"
+
+
+def test_create_fails_cleanly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        return
+    h = ctypes.c_void_p()
+    st = gj.lib().gj_create(ctypes.byref(h), 0, None)
+    assert st == gj.GJ_ERR_CUDA and not h.value

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Counts, offsets, multiplicities, summary levels and materialised rows are
+integers and must match bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_10435_gb300 import datagen as G
+from tests import golden_fig
+from tests.gpu_util import Run, check_canonical_window, device_columns, to_u64
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CAP = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10435_gb300 import gj
+    c = gj.Context(0)
+    yield c
+    c.close()
+
+
+def full_parity(ctx, q, check_levels=True, windows=()):
+    """Everything the oracle can materialise, compared exactly."""
+    run = Run(ctx, q)
+    c = O.count(q, rows=True)
+    total = run.summarize()
+    assert total == c.total
+    if total:
+        j = O.join(q)
+        ref_cols = O.columns(q, j.rowids)
+        cols, rids = run.rows()
+        assert np.array_equal(rids, j.rowids)
+        for a, b in zip(cols, ref_cols):
+            assert np.array_equal(a, b)
+        # arbitrary windows, including ragged tails and single rows
+        for (r0, n) in windows:
+            if r0 >= total:
+                continue
+            cw, rw = run.rows(r0, n)
+            m = min(n, total - r0)
+            assert np.array_equal(rw, j.rowids[r0:r0 + m])
+            for a, b in zip(cw, ref_cols):
+                assert np.array_equal(a, b[r0:r0 + m])
+        if check_levels:
+            lv = O.gfjs_levels(q, j.rowids)
+            for l in range(len(lv)):
+                val, freq, off = run.q.level(l, 0, total)
+                assert np.array_equal(val.cpu().numpy(), lv[l].value)
+                assert np.array_equal(to_u64(freq), lv[l].freq)
+                assert np.array_equal(to_u64(off), lv[l].offset)
+    # per key-tuple multiplicities
+    gm = O.group_mult_from_counts(q, c)
+    for rel in range(len(q.relations)):
+        tab = run.group_table(rel)
+        keys, mult = gm[rel]
+        assert len(tab) == keys.shape[0]
+        for k, m in zip(keys.tolist(), mult.tolist()):
+            assert tab[tuple(k)][1] == int(m), (rel, k)
+    run.close()
+    return total
+
+
+def test_figure1_on_gpu(ctx):
+    q, result, gfjs, _ = golden_fig.load()
+    run = Run(ctx, q)
+    assert run.summarize() == 32
+    cols, rids = run.rows()
+    assert list(zip(*[c.tolist() for c in cols])) == result
+    for l, name in enumerate("ABCD"):
+        val, freq, off = run.q.level(l, 0, 32)
+        assert list(zip(val.tolist(), to_u64(freq).tolist())) == gfjs[name]
+    t1 = run.group_table(0)
+    assert t1[(3, 3)] == (8, 8) and t1[(3, 4)] == (24, 24) and t1[(0, 0)] == (0, 0)
+    t2 = run.group_table(1)
+    assert t2[(4, 3)][1] == 16
+    run.close()
+
+
+def tiny_queries():
+    qs = []
+    for seed in range(160):
+        n_rel = 1 + seed % 5
+        qs.append(G.random_tree_query(seed, n_rel, max_rows=5 if n_rel <= 3 else 4,
+                                      domain=3 if n_rel <= 2 else 2, max_new=2,
+                                      min_rows=0 if seed % 7 == 0 else 1))
+    return qs
+
+
+@pytest.mark.parametrize("q", tiny_queries(), ids=lambda q: q.name)
+def test_tiny_random_trees(ctx, q):
+    full_parity(ctx, q, windows=[(0, 1), (1, 2), (3, 5)])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_small_random_trees_several_tiles(ctx, seed):
+    # a few thousand result rows: several emit/expand tiles and ragged tails
+    q = G.random_tree_query(1000 + seed, 2 + seed % 4, max_rows=60, domain=6, max_new=2,
+                            min_rows=20)
+    full_parity(ctx, q, windows=[(0, 1000), (999, 1025), (2047, 3001)])
+
+
+def test_chain3_uniform_full(ctx):
+    q = G.chain3_uniform()
+    total = full_parity(ctx, q, windows=[(0, 1 << 18), (1 << 18, 1 << 18), (777_777, 1 << 20)])
+    assert total == O.count(q).total
+
+
+@pytest.mark.parametrize("s", [0.0, 1.1, 1.5])
+def test_chain5_zipf_reduced(ctx, s):
+    q = G.chain5_zipf(rows=20_000, domain=20_000, s=s)
+    full_parity(ctx, q, check_levels=True, windows=[(12345, 100_000)])
+
+
+def test_star_reduced(ctx):
+    q = G.star_poisson(fact_rows=30_000, domain=10_000)
+    full_parity(ctx, q, windows=[(5, 4097)])
+
+
+def test_empty_relation(ctx):
+    q = G.chain3_uniform(rows=100, end_domain=10, mid_domain=5)
+    q.relations[1] = G.Relation("R2", [1, 2], [np.zeros(0, np.int32)] * 2, [np.zeros(0, np.int32)])
+    run = Run(ctx, q)
+    assert run.summarize() == 0
+    cols, rids = run.rows(0, 10)
+    assert all(c.shape[0] == 0 for c in cols)
+    run.close()
+
+
+def _all_equal_star(sizes, value=7):
+    rels = [G.Relation(f"R{i}", [0], [np.full(n, value, np.int32)]) for i, n in enumerate(sizes)]
+    return G.Query("allequal", rels)
+
+
+def test_largest_exact_count(ctx):
+    run = Run(ctx, _all_equal_star([2, 7, 7, 73, 127, 337, 92737, 649657]))
+    assert run.summarize() == (1 << 64) - 2
+    run.close()
+
+
+def test_overflow_reported(ctx):
+    from paper_2206_10435_gb300 import gj
+    for sizes in ([3, 5, 17, 257, 641, 65537, 6700417], [256] * 9):
+        run = Run(ctx, _all_equal_star(sizes))
+        with pytest.raises(gj.GJError) as e:
+            run.summarize()
+        assert e.value.status == gj.GJ_ERR_OVERFLOW
+        run.close()
+    q = G.chain5_zipf(rows=10**6, domain=10**5, aligned=True)
+    run = Run(ctx, q)
+    with pytest.raises(gj.GJError) as e:
+        run.summarize()
+    assert e.value.status == gj.GJ_ERR_OVERFLOW
+    run.close()
+
+
+def test_dead_branch_does_not_overflow(ctx):
+    rels = [G.Relation("R0", [0], [np.array([1, 1, 1], np.int32)])]
+    rels.append(G.Relation("R1", [0, 1], [np.full(256, 2, np.int32), np.zeros(256, np.int32)]))
+    for i in range(2, 9):
+        rels.append(G.Relation(f"R{i}", [1], [np.zeros(256, np.int32)]))
+    rels.append(G.Relation("R9", [0], [np.array([1, 2], np.int32)]))
+    run = Run(ctx, G.Query("dead", rels))
+    assert run.summarize() == 0
+    run.close()
+
+
+def test_rejects_cyclic_and_disconnected(ctx):
+    from paper_2206_10435_gb300 import gj
+    a = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
+    r = ctx.load_relation([a, a], [0, 1])
+    s = ctx.load_relation([a, a], [1, 2])
+    t = ctx.load_relation([a, a], [2, 0])
+    u = ctx.load_relation([a], [9])
+    with pytest.raises(gj.GJError) as e:
+        ctx.query([r, s, t])
+    assert e.value.status == gj.GJ_ERR_NOT_ACYCLIC
+    with pytest.raises(gj.GJError) as e:
+        ctx.query([r, u])
+    assert e.value.status == gj.GJ_ERR_INVALID
+    for x in (r, s, t, u):
+        ctx.release_relation(x)
+
+
+def test_factor_matches_stable_sort(ctx):
+    rng = np.random.default_rng(3)
+    n = 300_000
+    cols = [rng.integers(-5, 1 << 20, n, dtype=np.int32), rng.integers(-(1 << 31), (1 << 31) - 1, n,
+                                                                          dtype=np.int32),
+            rng.integers(0, 3, n, dtype=np.int32)]
+    dev = [torch.from_numpy(c).cuda() for c in cols]
+    rid = ctx.load_relation(dev, [0, 1, 2])
+    for order in ([0, 1, 2], [2, 0, 1], [1, 2, 0]):
+        perm, gstart, gkey = ctx.factor_export(rid, n, 3, order)
+        ref = np.lexsort([cols[c] for c in reversed(order)])   # stable
+        assert np.array_equal(perm.cpu().numpy(), ref)
+        srt = np.stack([cols[c][ref] for c in range(3)], axis=1)
+        head = np.ones(n, bool)
+        head[1:] = (srt[1:] != srt[:-1]).any(axis=1)
+        starts = np.flatnonzero(head)
+        assert np.array_equal(gstart.cpu().numpy()[:-1], starts)
+        assert int(gstart[-1]) == n
+        assert np.array_equal(gkey.cpu().numpy().T, srt[starts])
+    ctx.release_relation(rid)
+
+
+def _sampled_group_mult(q, c, run, rel, n_sample=2000, seed=0):
+    """Oracle multiplicities of a sample of the GPU's groups."""
+    R = q.relations[rel]
+    perm, gstart, gkey = run.ctx.factor_export(run.ids[rel], R.n_rows, len(R.keys),
+                                               run.factor_order(rel))
+    _, m, _ = run.q.summary_groups(rel)
+    keys = gkey.cpu().numpy().T
+    mult = to_u64(m)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(keys.shape[0], size=min(n_sample, keys.shape[0]), replace=False)
+    packed = np.zeros(R.n_rows, dtype=np.int64)
+    for col in R.keys:
+        packed = packed * (1 << 32) + (col.astype(np.int64) & 0xFFFFFFFF) if len(R.keys) <= 2 else None
+    want = {}
+    for g in pick.tolist():
+        pk = 0
+        for v in keys[g].tolist():
+            pk = pk * (1 << 32) + (v & 0xFFFFFFFF)
+        want[pk] = g
+    sel = np.isin(packed, np.array(list(want.keys()), dtype=np.int64))
+    rows = np.flatnonzero(sel)
+    acc = {}
+    for r, v in zip(rows.tolist(), c.mult[rel][rows].tolist()):
+        acc[int(packed[r])] = acc.get(int(packed[r]), 0) + int(v)
+    for pk, g in want.items():
+        assert acc.get(pk, 0) == int(mult[g])
+
+
+@pytest.mark.parametrize("scale", ["full"])
+def test_chain5_zipf_full_size(ctx, scale):
+    """5-chain, 10^7 rows per table, Zipf(1.1) over 10^6: exact total and
+    sampled multiplicities against the oracle's counting pass; windows of
+    2^28 rows checked by properties that pin them to the sorted result."""
+    q = G.chain5_zipf()
+    c = O.count(q, rows=True)
+    run = Run(ctx, q)
+    total = run.summarize()
+    assert total == c.total
+    for rel in range(5):
+        _sampled_group_mult(q, c, run, rel)
+    dev = device_columns(torch, q)
+    pl = O.plan(q)
+    W = 1 << 28
+    # first, a middle and the last (ragged) window
+    for r0 in (0, (total // 2 // W) * W, (total // W) * W):
+        out, rids = run.q.desummarize(r0, W, rowids=True)
+        check_canonical_window(torch, q, pl, dev, out, rids)
+        assert out[0].shape[0] == min(W, total - r0)
+    run.close()
+
+
+def test_star_full_size(ctx):
+    q = G.star_poisson()
+    c = O.count(q)
+    run = Run(ctx, q)
+    total = run.summarize()
+    assert total == c.total
+    dev = device_columns(torch, q)
+    pl = O.plan(q)
+    W = 1 << 28
+    last = None
+    done = 0
+    for r0 in range(0, total, W):
+        out, rids = run.q.desummarize(r0, W, rowids=True)
+        last = check_canonical_window(torch, q, pl, dev, out, rids, last)
+        done += out[0].shape[0]
+    assert done == total
+    run.close()
