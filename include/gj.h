@@ -215,6 +215,36 @@ gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
 gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
                          void *const *out_cols, uint32_t *const *rowid_cols, uint64_t *n_out);
 
+/*
+ * Factor construction without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory:
+ * a database engine or serving process that hands all device memory to its
+ * own pool (where cudaMalloc would fail or break the pool's accounting), or
+ * code on a latency-critical path where cudaMalloc/cudaFree would
+ * synchronise the device.
+ *
+ * Same result as gj_build_factors + gj_factor_export for `col_order`
+ * (NULL = declared order): perm_dev (uint32[n_rows]), gstart_dev (capacity
+ * n_rows + 1 entries; n_groups + 1 are written), gkey_dev (capacity
+ * n_keys * n_rows; column c of group g at gkey[c*n_groups + g]) and
+ * *n_groups.  key_cols is a host array of n_keys device pointers.  Work is
+ * enqueued on `cuda_stream` on `device`; the call synchronises that stream.
+ *
+ * All scratch lives in one fixed device array inside the library (about
+ * 6.7 MB, held on every device that loads the library until the process
+ * exits), so n_rows may not exceed GJ_NOALLOC_MAX_ROWS: larger inputs return
+ * GJ_ERR_INVALID before any work is enqueued.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call shares the array and
+ * keeps its last contents: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ */
+#define GJ_NOALLOC_MAX_ROWS (1 << 18)
+gj_status gj_factor_build_noalloc(int32_t device, void *cuda_stream, int64_t n_rows,
+                                  int32_t n_keys, const int32_t *const *key_cols,
+                                  const int32_t *col_order, uint32_t *perm_dev,
+                                  uint32_t *gstart_dev, int32_t *gkey_dev, int64_t *n_groups);
+
 #ifdef __cplusplus
 }
 #endif

@@ -264,3 +264,89 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
 }
 
 }  // namespace gj
+
+namespace gj {
+
+cudaError_t radix_sort_u64_u32_in(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits,
+                                  uint64_t *k2, uint32_t *v2, uint32_t *hist,
+                                  unsigned long long *status, int64_t status_tiles);
+cudaError_t scan_u32_in(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
+                        int64_t n, uint32_t *total_dev, void *state_mem, size_t state_bytes);
+
+// Factor construction of key columns `cols` (device, n rows) with every
+// scratch buffer supplied by the caller (no device allocation).  Writes
+// perm[n], gstart[G+1] and gkey[nk*G] (column c of group g at c*G + g) and
+// *G_out.  Same steps and kernels as factor_build.
+cudaError_t factor_build_in(Ctx &c, const int32_t *const *cols, int nk, int64_t n,
+                            const std::vector<int> &order, uint32_t *perm, uint32_t *gstart,
+                            int32_t *gkey, int64_t *G_out, const FactorScratch &s) {
+    *G_out = 0;
+    if (n == 0) return cudaMemsetAsync(gstart, 0, sizeof(uint32_t), c.stream);
+    ColSet all{};
+    all.ncol = nk;
+    for (int i = 0; i < nk; i++) all.col[i] = cols[i];
+    // 1. min/max per column, read back through host memory on the stack
+    k_minmax_init<<<1, 32, 0, c.stream>>>(nk, s.mm); c.launches++;
+    dim3 grid((unsigned)std::max(1, grid_for(c, n) / std::max(1, nk)), nk);
+    k_minmax<<<grid, FT, 0, c.stream>>>(all, n, s.mm); c.launches++;
+    GJ_CUDA_TRY(cudaGetLastError());
+    int32_t mm[2 * MAX_KEYS];
+    GJ_CUDA_TRY(cudaMemcpyAsync(mm, s.mm, sizeof(int32_t) * 2 * nk, cudaMemcpyDeviceToHost, c.stream));
+    GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    std::vector<int> bits(nk);
+    for (int i = 0; i < nk; i++) bits[i] = bits_of((uint32_t)((int64_t)mm[2 * i + 1] - (int64_t)mm[2 * i]));
+    // 2. packed words, least significant first, each sorted stably
+    std::vector<std::vector<int>> words;
+    {
+        std::vector<int> cur;
+        int used = 0;
+        for (int i = (int)order.size() - 1; i >= 0; i--) {
+            int col = order[i];
+            if (used + bits[col] > 64 && !cur.empty()) {
+                words.push_back(cur);
+                cur.clear();
+                used = 0;
+            }
+            cur.push_back(col);
+            used += bits[col];
+        }
+        if (!cur.empty()) words.push_back(cur);
+    }
+    bool first = true;
+    for (auto &wcols : words) {
+        PackSpec ps{};
+        ps.ncol = (int)wcols.size();
+        int shift = 0;
+        for (int i = 0; i < ps.ncol; i++) {
+            int col = wcols[i];
+            ps.col[i] = cols[col];
+            ps.mn[i] = mm[2 * col];
+            ps.shift[i] = shift;
+            shift += bits[col];
+        }
+        k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, first ? nullptr : perm, n, s.keys, perm); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        GJ_CUDA_TRY(radix_sort_u64_u32_in(c, s.keys, perm, n, shift, s.k2, s.v2, s.hist, s.status,
+                                          s.status_tiles));
+        first = false;
+    }
+    // 3. group heads and ids
+    if (words.size() == 1) {
+        k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(s.keys, n, s.head); c.launches++;
+    } else {
+        k_heads_gather<<<grid_for(c, n), FT, 0, c.stream>>>(all, perm, n, s.head); c.launches++;
+    }
+    GJ_CUDA_TRY(cudaGetLastError());
+    GJ_CUDA_TRY(scan_u32_in(c, nullptr, s.head, s.gid, n, s.gcount, s.scan_state, s.scan_state_bytes));
+    uint32_t G = 0;
+    GJ_CUDA_TRY(cudaMemcpyAsync(&G, s.gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
+    GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    // 4. group starts and key values
+    k_group_compact<<<grid_for(c, n), FT, 0, c.stream>>>(all, perm, s.head, s.gid, n, G, gstart,
+                                                         gkey); c.launches++;
+    GJ_CUDA_TRY(cudaGetLastError());
+    *G_out = G;
+    return cudaSuccess;
+}
+
+}  // namespace gj

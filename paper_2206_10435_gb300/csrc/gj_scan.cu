@@ -213,3 +213,36 @@ cudaError_t scan_u64_sat(Ctx &c, const uint64_t *in, const uint8_t *heads, uint6
 }
 
 }  // namespace gj
+
+namespace gj {
+
+// scan_u32 with the lookback state in caller memory (no device allocation):
+// state must hold scan_u32_state_bytes(n) bytes.
+size_t scan_u32_state_bytes(int64_t n) {
+    int64_t tiles = ceil_div(n > 0 ? n : 1, SCAN_THREADS * 16);
+    size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
+    return 16 + flag_bytes + 2 * (size_t)tiles * sizeof(uint32_t);
+}
+
+cudaError_t scan_u32_in(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
+                        int64_t n, uint32_t *total_dev, void *state_mem, size_t state_bytes) {
+    constexpr int TILE = SCAN_THREADS * 16;
+    if (n <= 0) {
+        if (total_dev) GJ_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), c.stream));
+        return cudaSuccess;
+    }
+    if (state_bytes < scan_u32_state_bytes(n)) return cudaErrorInvalidValue;
+    int64_t tiles = ceil_div(n, TILE);
+    size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
+    uint32_t *state = (uint32_t *)state_mem;
+    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 16 + flag_bytes, c.stream));
+    uint32_t *counter = state;
+    uint32_t *fl = state + 4;
+    uint32_t *agg = (uint32_t *)((char *)state + 16 + flag_bytes);
+    uint32_t *inc = agg + tiles;
+    k_scan<uint32_t, AddU32, 16, false><<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(
+        in, flags, nullptr, out, n, counter, fl, agg, inc, total_dev, nullptr, nullptr, c.err); c.launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace gj

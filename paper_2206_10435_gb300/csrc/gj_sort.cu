@@ -238,3 +238,45 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
 }
 
 }  // namespace gj
+
+namespace gj {
+
+// Same sort with every scratch buffer supplied by the caller (no device
+// allocation): k2/v2 hold n entries, hist 8*256 + 8 words, status
+// status_tiles*256 words (status_tiles >= ceil(n / 4096)).
+cudaError_t radix_sort_u64_u32_in(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits,
+                                  uint64_t *k2, uint32_t *v2, uint32_t *hist,
+                                  unsigned long long *status, int64_t status_tiles) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    if (n > 0x7fffffffLL || bits > 64) return cudaErrorInvalidValue;
+    const int passes = (bits + 7) / 8;
+    const int64_t tiles = ceil_div(n, RS_TILE);
+    if (tiles > status_tiles) return cudaErrorInvalidValue;
+    GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)RS_SMEM));
+    uint32_t *counters = hist + RS_MAX_PASSES * RS_RADIX;
+    GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + passes),
+                                c.stream));
+    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
+    if (hist_blocks < 1) hist_blocks = 1;
+    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
+    uint64_t *ka = keys, *kb = k2;
+    uint32_t *va = vals, *vb = v2;
+    for (int p = 0; p < passes; p++) {
+        GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
+                                    c.stream));
+        k_onesweep<<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
+            ka, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    if (ka != keys) {
+        GJ_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c.stream));
+        GJ_CUDA_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c.stream));
+    }
+    return cudaSuccess;
+}
+
+}  // namespace gj

@@ -25,6 +25,21 @@ struct Factor {
     std::vector<void *> pay;       // payloads in perm order (width*n bytes)
 };
 
+// Caller-supplied scratch of factor_build_in.
+struct FactorScratch {
+    uint64_t *keys, *k2;              // [n]
+    uint32_t *v2;                     // [n]
+    uint32_t *hist;                   // [8*256 + 8]
+    unsigned long long *status;       // [status_tiles * 256]
+    int64_t status_tiles;
+    uint8_t *head;                    // [n]
+    uint32_t *gid;                    // [n]
+    uint32_t *gcount;                 // [1]
+    void *scan_state;
+    size_t scan_state_bytes;
+    int32_t *mm;                      // [2 * MAX_KEYS]
+};
+
 struct Relation {
     int64_t n = 0;
     int nk = 0, np = 0;

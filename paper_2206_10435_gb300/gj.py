@@ -91,6 +91,10 @@ def lib() -> ctypes.CDLL:
         "gj_level": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
                                     _P, _P, _P, ctypes.c_uint64,
                                     ctypes.POINTER(ctypes.c_uint64)]),
+        "gj_factor_build_noalloc": (ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_int64,
+                                                   ctypes.c_int32, ctypes.POINTER(_P),
+                                                   ctypes.POINTER(ctypes.c_int32), _P, _P, _P,
+                                                   ctypes.POINTER(ctypes.c_int64)]),
         "gj_desummarize": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(_P), ctypes.POINTER(_P),
                                           ctypes.POINTER(ctypes.c_uint64)]),
