@@ -278,7 +278,9 @@ def main():
                 "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                 "bytes_per_launch": prof["emit_bytes"] / max(prof["emit_launches"], 1),
-                "avg_launch_ms": prof["emit_ms"] / max(prof["emit_launches"], 1)}
+                "avg_launch_ms": prof["emit_ms"] / max(prof["emit_launches"], 1),
+                "expand_ms_per_step": prof["expand_ms"] / a.steps,
+                "emit_ms_per_step": prof["emit_ms"] / a.steps}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a, q, a.cpu_sample_rows)

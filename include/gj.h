@@ -96,6 +96,8 @@ typedef struct {
     double emit_ms;          /* their summed device time, from CUDA events on the stream */
     uint64_t emit_rows;      /* result rows they wrote */
     uint64_t emit_bytes;     /* bytes of result columns they wrote */
+    double expand_ms;        /* time from the start to the end of the window expansions
+                                (Algorithm 4 restricted to each window), CUDA events */
 } gj_profile_t;
 
 /* Library version and status text. */

@@ -125,6 +125,19 @@ gj_status gj_create(gj_ctx **out, int32_t device, void *cuda_stream) {
         return GJ_ERR_OOM;
     }
     cudaMemset(c.err, 0, 16);
+    {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&c.pool, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            c.pool = nullptr;   // fall back to the device's default pool
+        }
+    }
     cudaDeviceSynchronize();
     *out = x;
     return GJ_OK;
@@ -141,8 +154,16 @@ gj_status gj_profile(gj_ctx *ctx, int32_t enable, gj_profile_t *out) {
             float t = 0;
             if (cudaEventElapsedTime(&t, c.ev_used[i], c.ev_used[i + 1]) == cudaSuccess) ms += t;
         }
+        double xms = 0;
+        for (size_t i = 0; i + 1 < c.xev_used.size(); i += 2) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, c.xev_used[i], c.xev_used[i + 1]) == cudaSuccess) xms += t;
+        }
         c.ev_free.insert(c.ev_free.end(), c.ev_used.begin(), c.ev_used.end());
+        c.ev_free.insert(c.ev_free.end(), c.xev_used.begin(), c.xev_used.end());
         c.ev_used.clear();
+        c.xev_used.clear();
+        out->expand_ms = xms;
         out->launches = c.launches;
         out->emit_launches = c.emit_launches;
         out->emit_ms = ms;
@@ -176,8 +197,10 @@ void gj_destroy(gj_ctx *ctx) {
     for (auto &kv : ctx->s.rels) relation_free(c, *kv.second);
     ctx->s.rels.clear();
     cudaStreamSynchronize(c.stream);
+    if (c.pool) cudaMemPoolDestroy(c.pool);
     for (cudaEvent_t e : c.ev_free) cudaEventDestroy(e);
     for (cudaEvent_t e : c.ev_used) cudaEventDestroy(e);
+    for (cudaEvent_t e : c.xev_used) cudaEventDestroy(e);
     cudaFree(c.err);
     cudaFreeHost(c.pinned);
     delete ctx;
@@ -211,7 +234,7 @@ gj_status gj_load_relation(gj_ctx *ctx, const gj_relation_desc *d, int32_t *rel_
         const int32_t *p = d->key_cols[i];
         if (copy && R->n > 0) {
             void *q = nullptr;
-            if (cudaMallocAsync(&q, 4 * R->n, c.stream) != cudaSuccess) { relation_free(c, *R); return GJ_ERR_OOM; }
+            if (dalloc_bytes(c, &q, 4 * R->n) != cudaSuccess) { relation_free(c, *R); return GJ_ERR_OOM; }
             R->owned.push_back(q);
             if (cudaMemcpyAsync(q, p, 4 * R->n, cudaMemcpyDefault, c.stream) != cudaSuccess) {
                 relation_free(c, *R);
@@ -227,7 +250,7 @@ gj_status gj_load_relation(gj_ctx *ctx, const gj_relation_desc *d, int32_t *rel_
         size_t bytes = (size_t)d->payload_width[i] * R->n;
         if (copy && R->n > 0) {
             void *q = nullptr;
-            if (cudaMallocAsync(&q, bytes, c.stream) != cudaSuccess) { relation_free(c, *R); return GJ_ERR_OOM; }
+            if (dalloc_bytes(c, &q, bytes) != cudaSuccess) { relation_free(c, *R); return GJ_ERR_OOM; }
             R->owned.push_back(q);
             if (cudaMemcpyAsync(q, p, bytes, cudaMemcpyDefault, c.stream) != cudaSuccess) {
                 relation_free(c, *R);

@@ -138,36 +138,37 @@ struct ExpandOut {
     uint64_t *unit;
 };
 
+// slot_first[t] = item owning output slot t*EXP_TILE (items own the slots
+// [excl[i], excl[i] + cnt[i]) of the next frontier); one scatter pass.
+__global__ void k_slot_first(const uint32_t *__restrict__ excl, const uint32_t *__restrict__ cnt,
+                             int64_t F, int64_t tiles, uint32_t *slot_first) {
+    for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
+        uint64_t lo = excl[i], hi = lo + cnt[i];
+        for (uint64_t t = (lo + EXP_TILE - 1) / EXP_TILE; t * EXP_TILE < hi && (int64_t)t < tiles; t++)
+            slot_first[t] = (uint32_t)i;
+    }
+}
+
 // Tile of EXP_TILE output slots per CTA; slot -> source item by a search of
 // the item offsets staged in shared memory (each item has >= 1 slot).
 __global__ void __launch_bounds__(DT)
 k_expand_write(ExpandSpec s, int64_t F, const uint32_t *__restrict__ excl, int64_t Fout,
+               const uint32_t *__restrict__ slot_first, int64_t tiles,
                const uint32_t *__restrict__ lo_in, const uint64_t *__restrict__ unit_in,
                ExpandOut o) {
     __shared__ uint32_t s_off[EXP_TILE + 1];
-    __shared__ int64_t s_first;
-    __shared__ int s_cnt;
-    const int64_t o0 = (int64_t)blockIdx.x * EXP_TILE;
+    const int64_t tile = blockIdx.x;
+    const int64_t o0 = tile * EXP_TILE;
     if (o0 >= Fout) return;
     const int64_t o1 = min((int64_t)Fout, o0 + EXP_TILE);
-    if (threadIdx.x == 0) {
-        // last item with excl <= o0, and last item with excl <= o1 - 1
-        int64_t a = 0, b = F;
-        while (a < b) { int64_t m = (a + b) >> 1; if (excl[m] <= (uint64_t)o0) a = m + 1; else b = m; }
-        int64_t first = a - 1;
-        a = first; b = F;
-        while (a < b) { int64_t m = (a + b) >> 1; if (excl[m] <= (uint64_t)(o1 - 1)) a = m + 1; else b = m; }
-        s_first = first;
-        int64_t cnt = a - first;
-        // every item owns >= 1 slot of the tile; anything else is a bug that
-        // must not write past the shared-memory staging
-        if (first < 0 || cnt > EXP_TILE) { raise_err(s.err, ERRF_BOUNDS); cnt = 0; }
-        s_cnt = (int)cnt;
+    const int64_t first = slot_first[tile];
+    const int64_t last = (tile + 1 < tiles) ? (int64_t)slot_first[tile + 1] : F - 1;
+    const int nitems = (int)(last - first + 1);
+    // every item owns >= 1 slot, so a tile sees at most EXP_TILE + 1 items
+    if (last < first || nitems > EXP_TILE + 1) {
+        if (threadIdx.x == 0) raise_err(s.err, ERRF_BOUNDS);
+        return;
     }
-    __syncthreads();
-    const int64_t first = s_first;
-    const int nitems = s_cnt;
-    if (nitems == 0) return;
     for (int t = threadIdx.x; t < nitems; t += DT) s_off[t] = excl[first + t];
     __syncthreads();
     const int j = s.depth;
@@ -331,9 +332,14 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         o.lh = nxt.lh;
         o.unit = nxt.unit;
         if (nxt.F > 0) {
-            k_expand_write<<<(unsigned)ceil_div(nxt.F, EXP_TILE), DT, 0, c.stream>>>(
-                s, cur.F, excl, nxt.F, lo, unit, o); c.launches++;
+            const int64_t tiles = ceil_div(nxt.F, EXP_TILE);
+            uint32_t *slot_first = nullptr;
+            GJ_CUDA_TRY(dalloc(c, &slot_first, tiles + 1));
+            k_slot_first<<<grid_for(c, cur.F), DT, 0, c.stream>>>(excl, cnt, cur.F, tiles, slot_first); c.launches++;
+            k_expand_write<<<(unsigned)tiles, DT, 0, c.stream>>>(
+                s, cur.F, excl, nxt.F, slot_first, tiles, lo, unit, o); c.launches++;
             GJ_CUDA_TRY(cudaGetLastError());
+            dfree(c, slot_first);
         }
         dfree(c, cnt);
         dfree(c, lo);
@@ -430,6 +436,234 @@ k_emit(EmitSpec e, int64_t B, uint64_t row0, int64_t n) {
     }
 }
 
+// Emission with 4 consecutive rows per thread.  The thread finds the block
+// of its first row by a search of the staged block offsets and splits that
+// row's offset into per-relation digits once; the next rows follow by
+// incrementing the digits like an odometer (rows of a block are ordered
+// r_1..r_k, relation k fastest), stepping to the next block when the
+// odometer wraps.  Output columns are grouped by the relation they come
+// from, so the group and position of that relation are compile-time
+// register indices; each column is written with one 16-byte streaming
+// store per thread when the buffers allow it.
+constexpr int EMIT_RPT = 4;
+constexpr int EMIT4_TILE = DT * EMIT_RPT;
+constexpr int MAXC = MAXV + MAXP;
+
+struct Emit4Spec {
+    const uint32_t *gstart[MAXR];    // by query position
+    const uint32_t *perm[MAXR];
+    uint32_t *rid_out[MAXR];
+    const uint32_t *grp[MAXR];       // frontier groups, by query position
+    int col_off[MAXR + 1];           // output columns of relation j: [col_off[j], col_off[j+1])
+    const void *src[MAXC];
+    void *dst[MAXC];
+    uint8_t kind[MAXC];              // 0 key (int32, by group), 1 payload int32, 2 payload int64
+    const uint64_t *A;
+    uint32_t *err;
+    int vec;                         // every destination is 16-byte aligned
+};
+
+// tile_first[t] = block holding the first row of emit tile t (rows
+// [row0 + t*T, ...)); written by the blocks themselves, one scatter pass.
+__global__ void k_tile_first(const uint64_t *__restrict__ A, int64_t B, uint64_t row0, int64_t n,
+                             int64_t tiles, uint32_t *tile_first) {
+    for (int64_t b = (int64_t)blockIdx.x * DT + threadIdx.x; b < B; b += (int64_t)gridDim.x * DT) {
+        uint64_t lo = A[b] > row0 ? A[b] - row0 : 0;
+        uint64_t hi = (b + 1 < B) ? A[b + 1] - row0 : (uint64_t)n;
+        int64_t t0 = (int64_t)((lo + EMIT4_TILE - 1) / EMIT4_TILE);
+        int64_t t1 = (int64_t)((hi + EMIT4_TILE - 1) / EMIT4_TILE);
+        for (int64_t t = t0; t < t1 && t < tiles; t++) tile_first[t] = (uint32_t)b;
+    }
+}
+
+// Writes one column of the warp's 128 rows (4 per lane, consecutive):
+// the values go through the warp's shared-memory slot and come back
+// transposed, so each store instruction covers 32 consecutive rows.
+// 32-bit values: one 16-byte shared store per lane (conflict-free); 64-bit
+// values: lane-major with one pad word per lane, so the 8-byte stores of a
+// half-warp hit distinct banks.
+__device__ __forceinline__ void emit_store_col(unsigned int *slot, const unsigned int (&v)[EMIT_RPT],
+                                               unsigned int *dst, int64_t wrow0, int64_t r1,
+                                               int lane) {
+    __syncwarp();
+    *(uint4 *)(slot + lane * EMIT_RPT) = make_uint4(v[0], v[1], v[2], v[3]);
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < EMIT_RPT; m++) {
+        int64_t r = wrow0 + m * 32 + lane;
+        if (r < r1) __stcs(dst + r, slot[m * 32 + lane]);
+    }
+}
+
+constexpr int SLOT64_STRIDE = EMIT_RPT + 1;
+
+__device__ __forceinline__ void emit_store_col(unsigned long long *slot,
+                                               const unsigned long long (&v)[EMIT_RPT],
+                                               unsigned long long *dst, int64_t wrow0, int64_t r1,
+                                               int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < EMIT_RPT; i++) slot[lane * SLOT64_STRIDE + i] = v[i];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < EMIT_RPT; m++) {
+        int q = m * 32 + lane;
+        int64_t r = wrow0 + q;
+        if (r < r1) __stcs(dst + r, slot[(q >> 2) * SLOT64_STRIDE + (q & 3)]);
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(DT)
+k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int64_t B,
+        uint64_t row0, int64_t n) {
+    __shared__ uint64_t s_A[EMIT4_TILE + 1];
+    __shared__ __align__(16) unsigned long long s_stage[DT / 32][32 * SLOT64_STRIDE];
+    const int64_t tile = blockIdx.x;
+    const int64_t r0 = tile * EMIT4_TILE;
+    if (r0 >= n) return;
+    const int64_t r1 = min(n, r0 + EMIT4_TILE);
+    const int64_t first = tile_first[tile];
+    const int64_t last = (tile + 1 < tiles) ? (int64_t)tile_first[tile + 1] : B - 1;
+    int nb = (int)(last - first + 1);
+    // the tile's rows plus the block holding the next tile's first row
+    if (last < first || nb > EMIT4_TILE + 1) {   // cannot happen: every block has >= 1 row
+        if (threadIdx.x == 0) raise_err(e.err, ERRF_BOUNDS);
+        return;
+    }
+    for (int t = threadIdx.x; t < nb; t += DT) s_A[t] = e.A[first + t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wrow0 = r0 + (int64_t)warp * 32 * EMIT_RPT;
+    const int64_t rbeg = r0 + (int64_t)threadIdx.x * EMIT_RPT;
+    // lanes past the end still take part in the warp's transposes
+    const int nrow = (int)max((int64_t)0, min((int64_t)EMIT_RPT, r1 - rbeg));
+    const uint64_t row = row0 + (uint64_t)rbeg;
+    // block of every row: a search for the first, then at most one step per row
+    int lb[EMIT_RPT];
+    if (nrow > 0) {
+        int a = 0, b = nb;
+        while (a < b) { int m = (a + b) >> 1; if (s_A[m] <= row) a = m + 1; else b = m; }
+        lb[0] = a - 1;
+    } else {
+        lb[0] = 0;
+    }
+#pragma unroll
+    for (int i = 1; i < EMIT_RPT; i++) {
+        lb[i] = lb[i - 1];
+        if (i < nrow && lb[i] + 1 < nb && s_A[lb[i] + 1] <= row + i) lb[i]++;
+    }
+    const uint64_t q0 = nrow > 0 ? row - s_A[lb[0]] : 0;
+    unsigned int *slot32 = (unsigned int *)s_stage[warp];
+    unsigned long long *slot64 = s_stage[warp];
+    // all group ids, then all group extents: two rounds of independent loads
+    uint32_t g[EMIT_RPT][K];
+#pragma unroll
+    for (int i = 0; i < EMIT_RPT; i++)
+#pragma unroll
+        for (int j = 0; j < K; j++) g[i][j] = __ldg(e.grp[j] + first + lb[i]);
+    // key columns need only the groups: write them while extents load
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        for (int c = e.col_off[j]; c < e.col_off[j + 1]; c++) {
+            if (e.kind[c] != 0) continue;
+            const unsigned int *src = (const unsigned int *)e.src[c];
+            unsigned int v[EMIT_RPT];
+#pragma unroll
+            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + g[i][j]);
+            emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
+        }
+    }
+    uint32_t pos[EMIT_RPT][K];
+    {
+        uint32_t base[EMIT_RPT][K], cnt[EMIT_RPT][K];
+#pragma unroll
+        for (int i = 0; i < EMIT_RPT; i++)
+#pragma unroll
+            for (int j = 0; j < K; j++) {
+                base[i][j] = __ldg(e.gstart[j] + g[i][j]);
+                cnt[i][j] = __ldg(e.gstart[j] + g[i][j] + 1) - base[i][j];
+            }
+        // digits of the first row (relation k-1 fastest), then an odometer
+        uint32_t d[K];
+        uint64_t q = q0;
+#pragma unroll
+        for (int j = K - 1; j >= 0; j--) {
+            uint32_t cj = cnt[0][j];
+            if (cj <= 1) { d[j] = 0; continue; }
+            if (q < 0x100000000ull) {
+                uint32_t q32 = (uint32_t)q;
+                d[j] = q32 % cj;
+                q = q32 / cj;
+            } else {
+                d[j] = (uint32_t)(q % cj);
+                q /= cj;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < K; j++) pos[0][j] = base[0][j] + d[j];
+#pragma unroll
+        for (int i = 1; i < EMIT_RPT; i++) {
+            if (lb[i] != lb[i - 1]) {
+#pragma unroll
+                for (int j = 0; j < K; j++) d[j] = 0;   // a block starts at digits 0
+            } else {
+                bool carry = true;
+#pragma unroll
+                for (int j = K - 1; j >= 0; j--) {
+                    if (carry) {
+                        d[j]++;
+                        carry = d[j] >= cnt[i][j];
+                        if (carry) d[j] = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < K; j++) pos[i][j] = base[i][j] + d[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        for (int c = e.col_off[j]; c < e.col_off[j + 1]; c++) {
+            const int kind = e.kind[c];
+            if (kind == 2) {
+                const unsigned long long *src = (const unsigned long long *)e.src[c];
+                unsigned long long v[EMIT_RPT];
+#pragma unroll
+                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                emit_store_col(slot64, v, (unsigned long long *)e.dst[c],
+                                                   wrow0, r1, lane);
+            } else if (kind == 1) {
+                const unsigned int *src = (const unsigned int *)e.src[c];
+                unsigned int v[EMIT_RPT];
+#pragma unroll
+                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
+            }
+        }
+        if (e.rid_out[j]) {
+            unsigned int v[EMIT_RPT];
+#pragma unroll
+            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
+            emit_store_col(slot32, v, e.rid_out[j], wrow0, r1, lane);
+        }
+    }
+}
+
+template <int K>
+cudaError_t launch_emit4(Ctx &c, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n) {
+    const int64_t tiles = ceil_div(n, EMIT4_TILE);
+    uint32_t *tile_first = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
+    k_tile_first<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(B, DT), (int64_t)c.num_sms * 16)),
+                   DT, 0, c.stream>>>(s.A, B, row0, n, tiles, tile_first); c.launches++;
+    if (c.prof) cudaEventRecord(c.event(), c.stream);
+    k_emit4<K><<<(unsigned)tiles, DT, 0, c.stream>>>(s, tile_first, tiles, B, row0, n); c.launches++;
+    cudaError_t e = cudaGetLastError();
+    dfree(c, tile_first);
+    return e;
+}
+
 // ------------------------------------------------------------------ levels
 
 struct LevelSpec {
@@ -503,46 +737,91 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
     if ((int)q.var_rel.size() > MAXV || (int)q.col_rel.size() > MAXP) return GJ_ERR_INVALID;
     if (!out_cols) return GJ_ERR_INVALID;
     Frontier f;
+    if (c.prof) cudaEventRecord(c.event(true), c.stream);
     cudaError_t e = expand(q, row0, row0 + n, q.k, false, f);
+    if (c.prof) cudaEventRecord(c.event(true), c.stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
-    EmitSpec s{};
-    s.k = q.k;
-    for (int j = 0; j < q.k; j++) {
-        s.preidx[j] = q.pos[j];
-        s.gstart[j] = q.r[j].F->gstart;
-        s.perm[j] = q.r[j].F->perm;
-        s.rid_out[j] = rowid_cols ? rowid_cols[j] : nullptr;
-        s.grp[j] = f.grp[j];
+    uint64_t width = 0;
+    for (int v = 0; v < (int)q.var_rel.size(); v++) width += 4;
+    for (size_t p = 0; p < q.col_rel.size(); p++) width += q.r[q.col_rel[p]].R->pw[q.col_pay[p]];
+    if (q.k > 8 && c.prof) cudaEventRecord(c.event(), c.stream);
+    if (q.k <= 8) {
+        Emit4Spec s{};
+        int nc = 0;
+        bool vec = true;
+        const int nv = (int)q.var_rel.size();
+        for (int j = 0; j < q.k; j++) {
+            s.gstart[j] = q.r[j].F->gstart;
+            s.perm[j] = q.r[j].F->perm;
+            s.rid_out[j] = rowid_cols ? rowid_cols[j] : nullptr;
+            s.grp[j] = f.grp[q.pos[j]];
+            s.col_off[j] = nc;
+            for (int v = 0; v < nv; v++) {
+                if (q.var_rel[v] != j) continue;
+                s.src[nc] = q.r[j].F->gkey + (int64_t)q.var_col[v] * q.r[j].F->G;
+                s.dst[nc] = out_cols[v];
+                s.kind[nc] = 0;
+                nc++;
+            }
+            for (size_t p = 0; p < q.col_rel.size(); p++) {
+                if (q.col_rel[p] != j) continue;
+                s.src[nc] = q.r[j].F->pay[q.col_pay[p]];
+                s.dst[nc] = out_cols[nv + p];
+                s.kind[nc] = q.r[j].R->pw[q.col_pay[p]] == 8 ? 2 : 1;
+                nc++;
+            }
+        }
+        s.col_off[q.k] = nc;
+        for (int i = 0; i < nc; i++) vec &= ((uintptr_t)s.dst[i] & 15) == 0;
+        s.vec = vec;
+        s.A = f.A;
+        s.err = c.err;
+        switch (q.k) {
+            case 1: e = launch_emit4<1>(c, s, f.F, row0, (int64_t)n); break;
+            case 2: e = launch_emit4<2>(c, s, f.F, row0, (int64_t)n); break;
+            case 3: e = launch_emit4<3>(c, s, f.F, row0, (int64_t)n); break;
+            case 4: e = launch_emit4<4>(c, s, f.F, row0, (int64_t)n); break;
+            case 5: e = launch_emit4<5>(c, s, f.F, row0, (int64_t)n); break;
+            case 6: e = launch_emit4<6>(c, s, f.F, row0, (int64_t)n); break;
+            case 7: e = launch_emit4<7>(c, s, f.F, row0, (int64_t)n); break;
+            default: e = launch_emit4<8>(c, s, f.F, row0, (int64_t)n); break;
+        }
+    } else {
+        EmitSpec s{};
+        s.k = q.k;
+        for (int j = 0; j < q.k; j++) {
+            s.preidx[j] = q.pos[j];
+            s.gstart[j] = q.r[j].F->gstart;
+            s.perm[j] = q.r[j].F->perm;
+            s.rid_out[j] = rowid_cols ? rowid_cols[j] : nullptr;
+            s.grp[j] = f.grp[j];
+        }
+        s.nv = (int)q.var_rel.size();
+        for (int v = 0; v < s.nv; v++) {
+            const QRel &t = q.r[q.var_rel[v]];
+            s.vkey[v] = t.F->gkey + (int64_t)q.var_col[v] * t.F->G;
+            s.vrel[v] = q.var_rel[v];
+            s.vout[v] = (int32_t *)out_cols[v];
+        }
+        s.np = (int)q.col_rel.size();
+        for (int p = 0; p < s.np; p++) {
+            const QRel &t = q.r[q.col_rel[p]];
+            s.pay[p] = t.F->pay[q.col_pay[p]];
+            s.prel[p] = q.col_rel[p];
+            s.pw[p] = t.R->pw[q.col_pay[p]];
+            s.pout[p] = out_cols[s.nv + p];
+        }
+        s.A = f.A;
+        s.err = c.err;
+        k_emit<<<(unsigned)ceil_div((int64_t)n, EMIT_TILE), DT, 0, c.stream>>>(s, f.F, row0, (int64_t)n); c.launches++;
+        e = cudaGetLastError();
     }
-    s.nv = (int)q.var_rel.size();
-    for (int v = 0; v < s.nv; v++) {
-        const QRel &t = q.r[q.var_rel[v]];
-        s.vkey[v] = t.F->gkey + (int64_t)q.var_col[v] * t.F->G;
-        s.vrel[v] = q.var_rel[v];
-        s.vout[v] = (int32_t *)out_cols[v];
-    }
-    s.np = (int)q.col_rel.size();
-    for (int p = 0; p < s.np; p++) {
-        const QRel &t = q.r[q.col_rel[p]];
-        s.pay[p] = t.F->pay[q.col_pay[p]];
-        s.prel[p] = q.col_rel[p];
-        s.pw[p] = t.R->pw[q.col_pay[p]];
-        s.pout[p] = out_cols[s.nv + p];
-    }
-    s.A = f.A;
-    s.err = c.err;
-    if (c.prof) cudaEventRecord(c.event(), c.stream);
-    k_emit<<<(unsigned)ceil_div((int64_t)n, EMIT_TILE), DT, 0, c.stream>>>(s, f.F, row0, (int64_t)n); c.launches++;
     if (c.prof) {
         cudaEventRecord(c.event(), c.stream);
         c.emit_launches++;
         c.emit_rows += n;
-        uint64_t width = 0;
-        for (int v = 0; v < s.nv; v++) width += 4;
-        for (int p = 0; p < s.np; p++) width += s.pw[p];
         c.emit_bytes += n * width;
     }
-    e = cudaGetLastError();
     frontier_free(c, f);
     if (e != cudaSuccess) return GJ_ERR_CUDA;
     gj_status st = check_device_error(c);

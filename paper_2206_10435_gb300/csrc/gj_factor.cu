@@ -173,7 +173,7 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
         GJ_CUDA_TRY(dalloc(c, &F.gkey, 1));
         for (int p = 0; p < R.np; p++) {
             void *d = nullptr;
-            GJ_CUDA_TRY(cudaMallocAsync(&d, 16, c.stream));
+            GJ_CUDA_TRY(dalloc_bytes(c, &d, 16));
             F.pay.push_back(d);
         }
         return cudaSuccess;
@@ -245,7 +245,7 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
     GJ_CUDA_TRY(cudaGetLastError());
     for (int p = 0; p < R.np; p++) {
         void *d = nullptr;
-        GJ_CUDA_TRY(cudaMallocAsync(&d, (size_t)R.pw[p] * n, c.stream));
+        GJ_CUDA_TRY(dalloc_bytes(c, &d, (size_t)R.pw[p] * n));
         if (R.pw[p] == 8) {
             k_gather<uint64_t><<<grid_for(c, n), FT, 0, c.stream>>>(
                 (const uint64_t *)R.pay[p], F.perm, n, (uint64_t *)d); c.launches++;

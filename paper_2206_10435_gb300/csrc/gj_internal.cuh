@@ -49,19 +49,23 @@ __device__ __forceinline__ void raise_err(uint32_t *err, uint32_t bits) {
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // stream-ordered pool owned by the context; it keeps freed memory for
+    // reuse instead of returning it to the driver at every synchronisation
+    cudaMemPool_t pool = nullptr;
     uint32_t *err = nullptr;          // device error word
     uint64_t *pinned = nullptr;       // small pinned host buffer for readbacks
     int num_sms = 0;
     uint64_t launches = 0;            // kernels launched (profiling)
     // device-time profile of the emit kernel (CUDA events on the stream)
     bool prof = false;
-    std::vector<cudaEvent_t> ev_free, ev_used;
+    std::vector<cudaEvent_t> ev_free, ev_used;     // emit kernel: start/stop pairs
+    std::vector<cudaEvent_t> xev_used;             // window expansion: start/stop pairs
     uint64_t emit_launches = 0, emit_rows = 0, emit_bytes = 0;
-    cudaEvent_t event() {
+    cudaEvent_t event(bool expansion = false) {
         cudaEvent_t e = nullptr;
         if (!ev_free.empty()) { e = ev_free.back(); ev_free.pop_back(); }
         else cudaEventCreate(&e);
-        ev_used.push_back(e);
+        (expansion ? xev_used : ev_used).push_back(e);
         return e;
     }
 };
@@ -71,7 +75,14 @@ template <class T>
 inline cudaError_t dalloc(Ctx &c, T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (c.pool) return cudaMallocFromPoolAsync((void **)p, count * sizeof(T), c.pool, c.stream);
     return cudaMallocAsync((void **)p, count * sizeof(T), c.stream);
+}
+inline cudaError_t dalloc_bytes(Ctx &c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (c.pool) return cudaMallocFromPoolAsync(p, bytes, c.pool, c.stream);
+    return cudaMallocAsync(p, bytes, c.stream);
 }
 template <class T>
 inline void dfree(Ctx &c, T *&p) {

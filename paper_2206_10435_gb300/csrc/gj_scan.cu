@@ -181,7 +181,7 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
     // layout: [counter][pad][flags (tiles)][values (tiles, 8-aligned)]
     size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
     size_t bytes = 16 + flag_bytes + 2 * (size_t)tiles * sizeof(T);
-    GJ_CUDA_TRY(cudaMallocAsync((void **)&state, bytes, c.stream));
+    GJ_CUDA_TRY(dalloc_bytes(c, (void **)&state, bytes));
     GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 16 + flag_bytes, c.stream));
     uint32_t *counter = state;
     uint32_t *flags = state + 4;

@@ -44,7 +44,7 @@ class RelationDesc(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("emit_launches", ctypes.c_uint64),
                 ("emit_ms", ctypes.c_double), ("emit_rows", ctypes.c_uint64),
-                ("emit_bytes", ctypes.c_uint64)]
+                ("emit_bytes", ctypes.c_uint64), ("expand_ms", ctypes.c_double)]
 
 
 class QuerySizes(ctypes.Structure):
