@@ -27,7 +27,7 @@
 // the relation that introduces the level's variable.
 #include <algorithm>
 
-#include "gj_state.cuh"
+#include "gj_emit.cuh"
 
 namespace gj {
 
@@ -436,234 +436,6 @@ k_emit(EmitSpec e, int64_t B, uint64_t row0, int64_t n) {
     }
 }
 
-// Emission with 4 consecutive rows per thread.  The thread finds the block
-// of its first row by a search of the staged block offsets and splits that
-// row's offset into per-relation digits once; the next rows follow by
-// incrementing the digits like an odometer (rows of a block are ordered
-// r_1..r_k, relation k fastest), stepping to the next block when the
-// odometer wraps.  Output columns are grouped by the relation they come
-// from, so the group and position of that relation are compile-time
-// register indices; each column is written with one 16-byte streaming
-// store per thread when the buffers allow it.
-constexpr int EMIT_RPT = 4;
-constexpr int EMIT4_TILE = DT * EMIT_RPT;
-constexpr int MAXC = MAXV + MAXP;
-
-struct Emit4Spec {
-    const uint32_t *gstart[MAXR];    // by query position
-    const uint32_t *perm[MAXR];
-    uint32_t *rid_out[MAXR];
-    const uint32_t *grp[MAXR];       // frontier groups, by query position
-    int col_off[MAXR + 1];           // output columns of relation j: [col_off[j], col_off[j+1])
-    const void *src[MAXC];
-    void *dst[MAXC];
-    uint8_t kind[MAXC];              // 0 key (int32, by group), 1 payload int32, 2 payload int64
-    const uint64_t *A;
-    uint32_t *err;
-    int vec;                         // every destination is 16-byte aligned
-};
-
-// tile_first[t] = block holding the first row of emit tile t (rows
-// [row0 + t*T, ...)); written by the blocks themselves, one scatter pass.
-__global__ void k_tile_first(const uint64_t *__restrict__ A, int64_t B, uint64_t row0, int64_t n,
-                             int64_t tiles, uint32_t *tile_first) {
-    for (int64_t b = (int64_t)blockIdx.x * DT + threadIdx.x; b < B; b += (int64_t)gridDim.x * DT) {
-        uint64_t lo = A[b] > row0 ? A[b] - row0 : 0;
-        uint64_t hi = (b + 1 < B) ? A[b + 1] - row0 : (uint64_t)n;
-        int64_t t0 = (int64_t)((lo + EMIT4_TILE - 1) / EMIT4_TILE);
-        int64_t t1 = (int64_t)((hi + EMIT4_TILE - 1) / EMIT4_TILE);
-        for (int64_t t = t0; t < t1 && t < tiles; t++) tile_first[t] = (uint32_t)b;
-    }
-}
-
-// Writes one column of the warp's 128 rows (4 per lane, consecutive):
-// the values go through the warp's shared-memory slot and come back
-// transposed, so each store instruction covers 32 consecutive rows.
-// 32-bit values: one 16-byte shared store per lane (conflict-free); 64-bit
-// values: lane-major with one pad word per lane, so the 8-byte stores of a
-// half-warp hit distinct banks.
-__device__ __forceinline__ void emit_store_col(unsigned int *slot, const unsigned int (&v)[EMIT_RPT],
-                                               unsigned int *dst, int64_t wrow0, int64_t r1,
-                                               int lane) {
-    __syncwarp();
-    *(uint4 *)(slot + lane * EMIT_RPT) = make_uint4(v[0], v[1], v[2], v[3]);
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < EMIT_RPT; m++) {
-        int64_t r = wrow0 + m * 32 + lane;
-        if (r < r1) __stcs(dst + r, slot[m * 32 + lane]);
-    }
-}
-
-constexpr int SLOT64_STRIDE = EMIT_RPT + 1;
-
-__device__ __forceinline__ void emit_store_col(unsigned long long *slot,
-                                               const unsigned long long (&v)[EMIT_RPT],
-                                               unsigned long long *dst, int64_t wrow0, int64_t r1,
-                                               int lane) {
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++) slot[lane * SLOT64_STRIDE + i] = v[i];
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < EMIT_RPT; m++) {
-        int q = m * 32 + lane;
-        int64_t r = wrow0 + q;
-        if (r < r1) __stcs(dst + r, slot[(q >> 2) * SLOT64_STRIDE + (q & 3)]);
-    }
-}
-
-template <int K>
-__global__ void __launch_bounds__(DT)
-k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int64_t B,
-        uint64_t row0, int64_t n) {
-    __shared__ uint64_t s_A[EMIT4_TILE + 1];
-    __shared__ __align__(16) unsigned long long s_stage[DT / 32][32 * SLOT64_STRIDE];
-    const int64_t tile = blockIdx.x;
-    const int64_t r0 = tile * EMIT4_TILE;
-    if (r0 >= n) return;
-    const int64_t r1 = min(n, r0 + EMIT4_TILE);
-    const int64_t first = tile_first[tile];
-    const int64_t last = (tile + 1 < tiles) ? (int64_t)tile_first[tile + 1] : B - 1;
-    int nb = (int)(last - first + 1);
-    // the tile's rows plus the block holding the next tile's first row
-    if (last < first || nb > EMIT4_TILE + 1) {   // cannot happen: every block has >= 1 row
-        if (threadIdx.x == 0) raise_err(e.err, ERRF_BOUNDS);
-        return;
-    }
-    for (int t = threadIdx.x; t < nb; t += DT) s_A[t] = e.A[first + t];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wrow0 = r0 + (int64_t)warp * 32 * EMIT_RPT;
-    const int64_t rbeg = r0 + (int64_t)threadIdx.x * EMIT_RPT;
-    // lanes past the end still take part in the warp's transposes
-    const int nrow = (int)max((int64_t)0, min((int64_t)EMIT_RPT, r1 - rbeg));
-    const uint64_t row = row0 + (uint64_t)rbeg;
-    // block of every row: a search for the first, then at most one step per row
-    int lb[EMIT_RPT];
-    if (nrow > 0) {
-        int a = 0, b = nb;
-        while (a < b) { int m = (a + b) >> 1; if (s_A[m] <= row) a = m + 1; else b = m; }
-        lb[0] = a - 1;
-    } else {
-        lb[0] = 0;
-    }
-#pragma unroll
-    for (int i = 1; i < EMIT_RPT; i++) {
-        lb[i] = lb[i - 1];
-        if (i < nrow && lb[i] + 1 < nb && s_A[lb[i] + 1] <= row + i) lb[i]++;
-    }
-    const uint64_t q0 = nrow > 0 ? row - s_A[lb[0]] : 0;
-    unsigned int *slot32 = (unsigned int *)s_stage[warp];
-    unsigned long long *slot64 = s_stage[warp];
-    // all group ids, then all group extents: two rounds of independent loads
-    uint32_t g[EMIT_RPT][K];
-#pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++)
-#pragma unroll
-        for (int j = 0; j < K; j++) g[i][j] = __ldg(e.grp[j] + first + lb[i]);
-    // key columns need only the groups: write them while extents load
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-        for (int c = e.col_off[j]; c < e.col_off[j + 1]; c++) {
-            if (e.kind[c] != 0) continue;
-            const unsigned int *src = (const unsigned int *)e.src[c];
-            unsigned int v[EMIT_RPT];
-#pragma unroll
-            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + g[i][j]);
-            emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
-        }
-    }
-    uint32_t pos[EMIT_RPT][K];
-    {
-        uint32_t base[EMIT_RPT][K], cnt[EMIT_RPT][K];
-#pragma unroll
-        for (int i = 0; i < EMIT_RPT; i++)
-#pragma unroll
-            for (int j = 0; j < K; j++) {
-                base[i][j] = __ldg(e.gstart[j] + g[i][j]);
-                cnt[i][j] = __ldg(e.gstart[j] + g[i][j] + 1) - base[i][j];
-            }
-        // digits of the first row (relation k-1 fastest), then an odometer
-        uint32_t d[K];
-        uint64_t q = q0;
-#pragma unroll
-        for (int j = K - 1; j >= 0; j--) {
-            uint32_t cj = cnt[0][j];
-            if (cj <= 1) { d[j] = 0; continue; }
-            if (q < 0x100000000ull) {
-                uint32_t q32 = (uint32_t)q;
-                d[j] = q32 % cj;
-                q = q32 / cj;
-            } else {
-                d[j] = (uint32_t)(q % cj);
-                q /= cj;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < K; j++) pos[0][j] = base[0][j] + d[j];
-#pragma unroll
-        for (int i = 1; i < EMIT_RPT; i++) {
-            if (lb[i] != lb[i - 1]) {
-#pragma unroll
-                for (int j = 0; j < K; j++) d[j] = 0;   // a block starts at digits 0
-            } else {
-                bool carry = true;
-#pragma unroll
-                for (int j = K - 1; j >= 0; j--) {
-                    if (carry) {
-                        d[j]++;
-                        carry = d[j] >= cnt[i][j];
-                        if (carry) d[j] = 0;
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < K; j++) pos[i][j] = base[i][j] + d[j];
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < K; j++) {
-        for (int c = e.col_off[j]; c < e.col_off[j + 1]; c++) {
-            const int kind = e.kind[c];
-            if (kind == 2) {
-                const unsigned long long *src = (const unsigned long long *)e.src[c];
-                unsigned long long v[EMIT_RPT];
-#pragma unroll
-                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(slot64, v, (unsigned long long *)e.dst[c],
-                                                   wrow0, r1, lane);
-            } else if (kind == 1) {
-                const unsigned int *src = (const unsigned int *)e.src[c];
-                unsigned int v[EMIT_RPT];
-#pragma unroll
-                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
-            }
-        }
-        if (e.rid_out[j]) {
-            unsigned int v[EMIT_RPT];
-#pragma unroll
-            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
-            emit_store_col(slot32, v, e.rid_out[j], wrow0, r1, lane);
-        }
-    }
-}
-
-template <int K>
-cudaError_t launch_emit4(Ctx &c, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n) {
-    const int64_t tiles = ceil_div(n, EMIT4_TILE);
-    uint32_t *tile_first = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
-    k_tile_first<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(B, DT), (int64_t)c.num_sms * 16)),
-                   DT, 0, c.stream>>>(s.A, B, row0, n, tiles, tile_first); c.launches++;
-    if (c.prof) cudaEventRecord(c.event(), c.stream);
-    k_emit4<K><<<(unsigned)tiles, DT, 0, c.stream>>>(s, tile_first, tiles, B, row0, n); c.launches++;
-    cudaError_t e = cudaGetLastError();
-    dfree(c, tile_first);
-    return e;
-}
-
 // ------------------------------------------------------------------ levels
 
 struct LevelSpec {
@@ -776,16 +548,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
         s.vec = vec;
         s.A = f.A;
         s.err = c.err;
-        switch (q.k) {
-            case 1: e = launch_emit4<1>(c, s, f.F, row0, (int64_t)n); break;
-            case 2: e = launch_emit4<2>(c, s, f.F, row0, (int64_t)n); break;
-            case 3: e = launch_emit4<3>(c, s, f.F, row0, (int64_t)n); break;
-            case 4: e = launch_emit4<4>(c, s, f.F, row0, (int64_t)n); break;
-            case 5: e = launch_emit4<5>(c, s, f.F, row0, (int64_t)n); break;
-            case 6: e = launch_emit4<6>(c, s, f.F, row0, (int64_t)n); break;
-            case 7: e = launch_emit4<7>(c, s, f.F, row0, (int64_t)n); break;
-            default: e = launch_emit4<8>(c, s, f.F, row0, (int64_t)n); break;
-        }
+        e = launch_emit(c, q.k, s, f.F, row0, (int64_t)n);
     } else {
         EmitSpec s{};
         s.k = q.k;

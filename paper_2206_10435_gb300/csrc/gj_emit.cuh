@@ -1,0 +1,35 @@
+// gj_emit.cuh -- the desummarise emit kernel's launch description.
+#pragma once
+
+#include "gj_state.cuh"
+
+namespace gj {
+
+constexpr int EMIT_DT = 256;
+constexpr int EMIT_MAXR = MAX_REL;
+constexpr int EMIT_MAXV = 32;
+constexpr int EMIT_MAXP = 32;
+constexpr int EMIT_RPT = 4;
+constexpr int EMIT4_TILE = EMIT_DT * EMIT_RPT;
+constexpr int MAXC = EMIT_MAXV + EMIT_MAXP;
+
+struct Emit4Spec {
+    const uint32_t *gstart[EMIT_MAXR];    // by query position
+    const uint32_t *perm[EMIT_MAXR];
+    uint32_t *rid_out[EMIT_MAXR];
+    const uint32_t *grp[EMIT_MAXR];       // frontier groups, by query position
+    int col_off[EMIT_MAXR + 1];           // output columns of relation j: [col_off[j], col_off[j+1])
+    const void *src[MAXC];
+    void *dst[MAXC];
+    uint8_t kind[MAXC];              // 0 key (int32, by group), 1 payload int32, 2 payload int64
+    const uint64_t *A;
+    uint32_t *err;
+    int vec;                         // every destination is 16-byte aligned
+};
+
+
+// Emits result rows [row0, row0 + n) from the block list A (B blocks): a
+// tile-to-block scatter, then the emit kernel for K = k relations (k <= 8).
+cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n);
+
+}  // namespace gj
