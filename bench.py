@@ -37,6 +37,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gj", choices=["gj", "reference"])
+    p.add_argument("--workload", default="chain5_zipf",
+                   choices=["chain5_zipf", "chain3_uniform", "star_poisson"])
     p.add_argument("--rows", type=int, default=10**7)
     p.add_argument("--domain", type=int, default=10**6)
     p.add_argument("--zipf", type=float, default=1.1)
@@ -45,11 +47,20 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-sample-rows", type=int, default=20000)
+    p.add_argument("--cpu-sample-rows", type=int, default=None,
+                   help="root rows kept for the oracle sample (default per workload)")
     return p.parse_args()
 
 
 def workload_name(a):
+    if a.workload == "chain3_uniform":
+        return ("chain3_uniform: R1(A,B) R2(B,C) R3(C,D), 10^4 rows/table, int32 keys, A,D "
+                "uniform over [0,10^4), B,C uniform over [0,1000), int32 payload/table, "
+                f"desummarised in 2^{a.chunk_log2}-row chunks")
+    if a.workload == "star_poisson":
+        return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
+                "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "
+                f"desummarised in 2^{a.chunk_log2}-row chunks")
     return (f"chain5_zipf: 5-table chain R_i(K_i-1,K_i), {a.rows} rows/table, int32 keys "
             f"Zipf({a.zipf}) over [0,{a.domain}), int64 payload/table, "
             f"desummarised in 2^{a.chunk_log2}-row chunks")
@@ -57,6 +68,10 @@ def workload_name(a):
 
 def make_query(a, rank):
     from paper_2206_10435_gb300 import datagen as G
+    if a.workload == "chain3_uniform":
+        return G.chain3_uniform(seed=G.SEED_BASE + 0 + 1000 * rank)
+    if a.workload == "star_poisson":
+        return G.star_poisson(seed=G.SEED_BASE + 2 + 1000 * rank)
     return G.chain5_zipf(seed=G.SEED_BASE + 1 + 1000 * rank, rows=a.rows, domain=a.domain,
                          s=a.zipf)
 
@@ -125,6 +140,33 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+EMIT_PROFILE = os.path.join(ROOT, "profiles", "k_emit4_chain5_zipf.md")
+EMIT_SOURCE = os.path.join(ROOT, "paper_2206_10435_gb300", "csrc", "gj_emit.cu")
+
+
+def emit_traffic_per_row():
+    """DRAM bytes (read + write) per result row of the emit kernel, from the
+    committed ncu summary, or None if the kernel source changed since that
+    capture (its sha256 no longer matches)."""
+    import hashlib
+    try:
+        text = open(EMIT_PROFILE).read()
+        src = hashlib.sha256(open(EMIT_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None, "no ncu summary"
+    fields = {}
+    for line in text.splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_sha256") != src:
+        return None, "kernel changed since the ncu capture"
+    try:
+        return float(fields["dram_bytes_per_row"]), "ncu capture, scaled by rows per launch"
+    except (KeyError, ValueError):
+        return None, "no traffic in the ncu summary"
+
+
 def cpu_baseline(a, q_full, sample_rows):
     """The oracle, as it stands, on a bounded sample: the same tables with
     the root restricted to its first `sample_rows` rows (a sub-join of the
@@ -173,8 +215,13 @@ def run_reference(a, rank, world):
     print(json.dumps(out), flush=True)
 
 
+DEFAULT_SAMPLE = {"chain5_zipf": 20000, "chain3_uniform": 10**4, "star_poisson": 10**6}
+
+
 def main():
     a = parse()
+    if a.cpu_sample_rows is None:
+        a.cpu_sample_rows = DEFAULT_SAMPLE[a.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -273,9 +320,13 @@ def main():
 
     peak, peak_kind = measured_peaks()
     achieved = (prof["emit_bytes"] / (prof["emit_ms"] * 1e6)) if prof["emit_ms"] else None
-    roofline = {"bound": "hbm", "kernel": "k_emit (desummarise emit)",
+    tpr, tnote = emit_traffic_per_row() if a.workload == "chain5_zipf" else (None, "captured for chain5_zipf only")
+    rows_per_launch = prof["emit_rows"] / max(prof["emit_launches"], 1)
+    traffic = tpr * rows_per_launch if tpr is not None else None
+    roofline = {"bound": "hbm", "kernel": "k_emit4 (desummarise emit)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_note": tnote,
                 "peak_kind": f"{peak_kind} hbm_gbs (burst copy)",
                 "bytes_per_launch": prof["emit_bytes"] / max(prof["emit_launches"], 1),
                 "avg_launch_ms": prof["emit_ms"] / max(prof["emit_launches"], 1),
@@ -287,7 +338,7 @@ def main():
         cpu.pop("seconds")
         cpu.pop("tuples")
     if rank == 0:
-        row_bytes = sum(4 for _ in range(6)) + 8 * 5
+        row_bytes = int(prof["emit_bytes"] // max(prof["emit_rows"], 1))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
