@@ -103,6 +103,8 @@ typedef struct {
 /* Library version and status text. */
 const char *gj_status_str(gj_status s);
 int32_t gj_version(void);
+/* The last CUDA failure seen by this thread: error name, text, source line. */
+const char *gj_last_error(void);
 
 /*
  * Creates a context on CUDA device `device` that enqueues its work on
@@ -216,6 +218,39 @@ gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
  */
 gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
                          void *const *out_cols, uint32_t *const *rowid_cols, uint64_t *n_out);
+
+/*
+ * Batched summaries: many independent queries at once.  The paper has one
+ * query at a time; the batch runs the same upward pass (Algorithm 2, the
+ * root marginal summing to |Q|, Section 3.3) for every query together, so
+ * its cost is a fixed sequence of about 30 kernels instead of tens of
+ * launches and several synchronisations per query.
+ *
+ * gj_batch_create plans queries q = 0..n_queries-1, query q being the
+ * relations rel_ids[query_off[q] .. query_off[q+1]) (root first, same tree
+ * rules as gj_query_create).  Restrictions: one or two key columns per
+ * relation, one shared attribute between a relation and its parent, at most
+ * 4 children per relation, at most 2^32 - 1 rows in all.  Planning reads the
+ * key ranges (one synchronisation) and allocates the workspace; relations
+ * must stay loaded and unchanged while the batch lives.
+ *
+ * gj_batch_run enqueues the whole summary on the context's stream without
+ * any synchronisation and writes |Q| (UINT64_MAX on overflow) to
+ * totals_dev[q] and GJ_OK / GJ_ERR_OVERFLOW to status_dev[q] (may be NULL).
+ * With use_graph != 0 the sequence is captured into a CUDA graph on the
+ * first call (and again when the outputs or parameters change) and each
+ * call is one graph launch.
+ */
+typedef struct gj_batch gj_batch;
+#define GJ_BATCH_GRID_MULT 1   /* persistent grids = SMs x this (1..64, default 4) */
+gj_status gj_batch_create(gj_ctx *ctx, const int32_t *rel_ids, const int32_t *query_off,
+                          int32_t n_queries, gj_batch **out);
+gj_status gj_batch_set(gj_batch *batch, int32_t param, int64_t value);
+gj_status gj_batch_info(gj_batch *batch, int64_t *n_rows, int32_t *n_relations, int32_t *levels,
+                        int32_t *key_bits);
+gj_status gj_batch_run(gj_batch *batch, int32_t use_graph, uint64_t *totals_dev,
+                       int32_t *status_dev);
+void gj_batch_destroy(gj_batch *batch);
 
 /*
  * Factor construction without any device allocation.  The paper has no

@@ -1,5 +1,6 @@
 // gj_api.cu -- the C ABI of include/gj.h: contexts, relations, the join-tree
 // planner and the entry points of the three steps.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -18,6 +19,14 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
                       uint32_t *const *rowid_cols, uint64_t *n_out);
 gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, int32_t *val,
                      uint64_t *freq, uint64_t *off, uint64_t cap, uint64_t *n_out);
+
+static thread_local char g_last_error[256] = "";
+
+void note_cuda_error(cudaError_t e, const char *file, int line) {
+    const char *base = strrchr(file, '/');
+    snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at %s:%d", cudaGetErrorName(e),
+             cudaGetErrorString(e), base ? base + 1 : file, line);
+}
 
 gj_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return GJ_OK;
@@ -102,6 +111,8 @@ const char *gj_status_str(gj_status s) {
 }
 
 int32_t gj_version(void) { return 1; }
+
+const char *gj_last_error(void) { return gj::g_last_error; }
 
 gj_status gj_create(gj_ctx **out, int32_t device, void *cuda_stream) {
     if (!out) return GJ_ERR_INVALID;

@@ -115,10 +115,16 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
 // ------------------------------------------------------------------ helpers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-#define GJ_CUDA_TRY(expr)                        \
-    do {                                         \
-        cudaError_t _e = (expr);                 \
-        if (_e != cudaSuccess) return _e;        \
+// Records the failing CUDA call (error name, file, line) for gj_last_error.
+void note_cuda_error(cudaError_t e, const char *file, int line);
+
+#define GJ_CUDA_TRY(expr)                                        \
+    do {                                                         \
+        cudaError_t _e = (expr);                                 \
+        if (_e != cudaSuccess) {                                 \
+            ::gj::note_cuda_error(_e, __FILE__, __LINE__);       \
+            return _e;                                           \
+        }                                                        \
     } while (0)
 
 }  // namespace gj

@@ -64,11 +64,12 @@ __global__ void __launch_bounds__(RS_RADIX) k_hist_to_base(uint32_t *hist) {
     h[d] = s[d] - h[d];
 }
 
+template <bool VALS>
 __global__ void __launch_bounds__(RS_THREADS)
-k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
-           const uint32_t *__restrict__ bucket_base, uint32_t *tile_counter,
-           unsigned long long *status, uint32_t *err) {
+k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
+             const uint32_t *__restrict__ bucket_base, uint32_t *tile_counter,
+             unsigned long long *status, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = (uint64_t *)smem;                              // RS_TILE
     uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);                // RS_TILE
@@ -91,7 +92,7 @@ k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         int64_t idx = wbase + i * 32 + lane;
-        if (idx < n) { k[i] = kin[idx]; v[i] = vin[idx]; }
+        if (idx < n) { k[i] = kin[idx]; v[i] = VALS ? vin[idx] : 0u; }
         else { k[i] = 0; v[i] = 0; }
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -167,7 +168,7 @@ k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
             uint32_t dg = (uint32_t)((k[i] >> shift) & 0xff);
             uint32_t pos = s_tile_off[dg] + s_whist[warp * RS_RADIX + dg] + rank[i];
             s_keys[pos] = k[i];
-            s_vals[pos] = v[i];
+            if (VALS) s_vals[pos] = v[i];
         }
     }
     __syncthreads();
@@ -180,10 +181,13 @@ k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
             uint32_t dg = (uint32_t)((key >> shift) & 0xff);
             uint32_t dest = s_glob[dg] + (uint32_t)(p - s_tile_off[dg]);
             kout[dest] = key;
-            vout[dest] = s_vals[p];
+            if (VALS) vout[dest] = s_vals[p];
         }
     }
 }
+
+// the (key, value) form used by factor construction
+constexpr auto k_onesweep = k_onesweep_t<true>;
 
 constexpr size_t RS_SMEM = (size_t)RS_TILE * 8 + (size_t)RS_TILE * 4 +
                            (size_t)RS_WARPS * RS_RADIX * 4 + 2 * RS_RADIX * 4 + 8 * 4;
@@ -276,6 +280,49 @@ cudaError_t radix_sort_u64_u32_in(Ctx &c, uint64_t *keys, uint32_t *vals, int64_
         GJ_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c.stream));
         GJ_CUDA_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c.stream));
     }
+    return cudaSuccess;
+}
+
+}  // namespace gj
+
+namespace gj {
+
+// Sets the keys-only sort kernel's shared-memory limit; call once before
+// any capture of radix_sort_keys_u64_in.
+cudaError_t radix_sort_keys_prepare() {
+    return cudaFuncSetAttribute(k_onesweep_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)RS_SMEM);
+}
+
+// Keys-only sort with caller scratch (no allocation, capturable in a CUDA
+// graph): k2 holds n keys, hist 8*256 + 8 words, status status_tiles*256
+// words.  Accepts up to 2^32 - 1 keys.
+cudaError_t radix_sort_keys_u64_in(Ctx &c, uint64_t *keys, int64_t n, int bits, uint64_t *k2,
+                                   uint32_t *hist, unsigned long long *status,
+                                   int64_t status_tiles) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    if (n > 0xffffffffLL || bits > 64) return cudaErrorInvalidValue;
+    const int passes = (bits + 7) / 8;
+    const int64_t tiles = ceil_div(n, RS_TILE);
+    if (tiles > status_tiles) return cudaErrorInvalidValue;
+    uint32_t *counters = hist + RS_MAX_PASSES * RS_RADIX;
+    GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + passes),
+                                c.stream));
+    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
+    if (hist_blocks < 1) hist_blocks = 1;
+    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
+    uint64_t *ka = keys, *kb = k2;
+    for (int p = 0; p < passes; p++) {
+        GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
+                                    c.stream));
+        k_onesweep_t<false><<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
+            ka, nullptr, kb, nullptr, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        std::swap(ka, kb);
+    }
+    if (ka != keys)
+        GJ_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c.stream));
     return cudaSuccess;
 }
 

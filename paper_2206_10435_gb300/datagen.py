@@ -215,3 +215,47 @@ def random_tree_query(seed: int, n_rel: int, max_rows: int = 6, domain: int = 3,
             pays = [_payload(rng, n, np.int32), _payload(rng, n, np.int64)]
         rels.append(Relation(f"T{j}", attrs, cols, pays))
     return Query(f"tree{seed}", rels, {a: f"X{a}" for a in range(next_attr)})
+
+
+def batch_queries_torch(seed: int = SEED_BASE + 3, n_queries: int = 4096,
+                        min_tables: int = 3, max_tables: int = 6,
+                        rows_range=(10**3, 10**6), domain_range=(10**2, 10**5),
+                        s_range=(0.0, 1.5), device="cuda"):
+    """The batch_queries distribution drawn on a CUDA device with torch (for
+    batches of billions of rows).  Returns a list of queries, each a list of
+    (attrs, [key tensors]) relations; no payloads."""
+    import torch
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lo_r, hi_r = np.log(rows_range[0]), np.log(rows_range[1])
+    lo_d, hi_d = np.log(domain_range[0]), np.log(domain_range[1])
+    cdfs = {}
+
+    def keys(n, s, D):
+        if s == 0.0:
+            return torch.randint(0, D, (n,), generator=g, device=device, dtype=torch.int32)
+        cdf = cdfs.get((s, D))
+        if cdf is None:
+            p = torch.arange(1, D + 1, device=device, dtype=torch.float64) ** (-s)
+            cdf = torch.cumsum(p, 0)
+            cdf /= cdf[-1].clone()
+            cdfs.clear()
+            cdfs[(s, D)] = cdf
+        u = torch.rand(n, generator=g, device=device, dtype=torch.float64)
+        r = torch.searchsorted(cdf, u, right=True).clamp_(max=D - 1)
+        perm = torch.randperm(D, generator=g, device=device)
+        return perm[r].to(torch.int32)
+
+    out = []
+    for _ in range(n_queries):
+        k = int(rng.integers(min_tables, max_tables + 1))
+        rows = np.exp(rng.uniform(lo_r, hi_r, size=k)).astype(np.int64)
+        doms = np.exp(rng.uniform(lo_d, hi_d, size=k + 1)).astype(np.int64)
+        s = float(rng.uniform(*s_range))
+        rels = []
+        for i in range(k):
+            n = int(rows[i])
+            rels.append(([i, i + 1], [keys(n, s, int(doms[i])), keys(n, s, int(doms[i + 1]))]))
+        out.append(rels)
+    return out

@@ -28,7 +28,10 @@ SAT = (1 << 64) - 1
 class GJError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        super().__init__(f"{what}: {_lib.gj_status_str(status).decode()} (status {status})")
+        msg = f"{what}: {_lib.gj_status_str(status).decode()} (status {status})"
+        if status == GJ_ERR_CUDA:
+            msg += f" [{_lib.gj_last_error().decode()}]"
+        super().__init__(msg)
 
 
 class RelationDesc(ctypes.Structure):
@@ -72,6 +75,7 @@ def lib() -> ctypes.CDLL:
     sig = {
         "gj_status_str": (ctypes.c_char_p, [ctypes.c_int]),
         "gj_version": (ctypes.c_int32, []),
+        "gj_last_error": (ctypes.c_char_p, []),
         "gj_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P]),
         "gj_destroy": (None, [_P]),
         "gj_set_stream": (ctypes.c_int, [_P, _P]),
@@ -95,6 +99,16 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.c_int32, ctypes.POINTER(_P),
                                                    ctypes.POINTER(ctypes.c_int32), _P, _P, _P,
                                                    ctypes.POINTER(ctypes.c_int64)]),
+        "gj_batch_create": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                           ctypes.POINTER(_P)]),
+        "gj_batch_set": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+        "gj_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]),
+        "gj_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+        "gj_batch_destroy": (None, [_P]),
         "gj_desummarize": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(_P), ctypes.POINTER(_P),
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -302,6 +316,53 @@ class Query:
         if rowids:
             return res, [t[:k] for t in rid_t]
         return res
+
+
+GJ_BATCH_GRID_MULT = 1
+
+
+class Batch:
+    """Many queries summarised together (gj_batch_*)."""
+
+    def __init__(self, ctx: Context, queries_rel_ids):
+        self.ctx = ctx
+        flat = [r for q in queries_rel_ids for r in q]
+        off = [0]
+        for q in queries_rel_ids:
+            off.append(off[-1] + len(q))
+        h = _P()
+        _check(lib().gj_batch_create(ctx.h, _i32(flat), _i32(off), len(queries_rel_ids),
+                                     ctypes.byref(h)), "gj_batch_create")
+        self.h = h
+        self.n_queries = len(queries_rel_ids)
+        n = ctypes.c_int64()
+        r, l, kb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().gj_batch_info(h, ctypes.byref(n), ctypes.byref(r), ctypes.byref(l),
+                                   ctypes.byref(kb)), "gj_batch_info")
+        self.n_rows, self.n_relations, self.levels, self.key_bits = n.value, r.value, l.value, kb.value
+        torch = ctx.torch
+        dev = torch.device("cuda", ctx.device)
+        self.totals = torch.zeros(self.n_queries, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(self.n_queries, dtype=torch.int32, device=dev)
+
+    def set_grid_mult(self, m: int):
+        _check(lib().gj_batch_set(self.h, GJ_BATCH_GRID_MULT, m), "gj_batch_set")
+
+    def run(self, use_graph: bool = True):
+        """Enqueue the batch (no synchronisation); results in .totals/.status."""
+        _check(lib().gj_batch_run(self.h, int(use_graph), _P(_ptr(self.totals)),
+                                  _P(_ptr(self.status))), "gj_batch_run")
+
+    def close(self):
+        if self.h:
+            lib().gj_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def load_query(ctx: Context, query, flags: int = GJ_REL_BORROW) -> list:
