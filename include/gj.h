@@ -171,6 +171,16 @@ void gj_query_destroy(gj_query *q);
 gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out);
 
 /*
+ * Runs this query's later work (summarise, levels, desummarise, destroy) on
+ * its own stream with its own readback buffer and error word, sharing the
+ * context's relations, factors and memory pool.  Different queries may then
+ * be driven from different host threads at the same time and their kernels
+ * overlap on the device.  Loading, releasing, factor building and query
+ * creation are serialised by a lock inside the context.
+ */
+gj_status gj_query_set_stream(gj_query *q, void *cuda_stream);
+
+/*
  * Summarisation: the upward sum-product pass of Algorithm 2 over the join
  * tree in the counting semiring (Eqs. 4-10: product of a relation's
  * frequencies with its children's messages, summed out over the separator),

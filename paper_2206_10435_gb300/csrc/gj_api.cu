@@ -218,6 +218,8 @@ void gj_destroy(gj_ctx *ctx) {
 }
 
 gj_status gj_load_relation(gj_ctx *ctx, const gj_relation_desc *d, int32_t *rel_id) {
+    if (!ctx) return GJ_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
     if (!ctx || !d || !rel_id) return GJ_ERR_INVALID;
     if (d->n_rows < 0 || d->n_rows > 0x7fffffffLL) return GJ_ERR_INVALID;
     if (d->n_keys < 1 || d->n_keys > MAX_KEYS) return GJ_ERR_INVALID;
@@ -279,6 +281,8 @@ gj_status gj_load_relation(gj_ctx *ctx, const gj_relation_desc *d, int32_t *rel_
 
 gj_status gj_release_relation(gj_ctx *ctx, int32_t rel_id) {
     if (!ctx) return GJ_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
+    if (!ctx) return GJ_ERR_INVALID;
     auto it = ctx->s.rels.find(rel_id);
     if (it == ctx->s.rels.end()) return GJ_ERR_INVALID;
     DeviceGuard g(ctx->s.c.device);
@@ -288,6 +292,8 @@ gj_status gj_release_relation(gj_ctx *ctx, int32_t rel_id) {
 }
 
 gj_status gj_build_factors(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order) {
+    if (!ctx) return GJ_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
     if (!ctx) return GJ_ERR_INVALID;
     auto it = ctx->s.rels.find(rel_id);
     if (it == ctx->s.rels.end()) return GJ_ERR_INVALID;
@@ -302,6 +308,8 @@ gj_status gj_build_factors(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
 gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order,
                            int64_t *n_groups, uint32_t *perm_dev, uint32_t *gstart_dev,
                            int32_t *gkey_dev) {
+    if (!ctx) return GJ_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
     if (!ctx || !n_groups) return GJ_ERR_INVALID;
     auto it = ctx->s.rels.find(rel_id);
     if (it == ctx->s.rels.end()) return GJ_ERR_INVALID;
@@ -324,6 +332,8 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
 }
 
 gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out) {
+    if (!ctx) return GJ_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
     if (!ctx || !rel_ids || !out || n_rel < 1 || n_rel > MAX_REL) return GJ_ERR_INVALID;
     *out = nullptr;
     std::unique_ptr<gj_query> qq(new gj_query());
@@ -397,8 +407,41 @@ gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj
 void gj_query_destroy(gj_query *q) {
     if (!q) return;
     DeviceGuard g(q->s.cs->c.device);
-    query_free_summary(q->s.cs->c, q->s);
+    query_free_summary(q->s.ctx(), q->s);
+    if (q->s.own) {
+        Ctx &o = *q->s.own;
+        cudaStreamSynchronize(o.stream);
+        cudaFree(o.err);
+        cudaFreeHost(o.pinned);
+    }
     delete q;
+}
+
+gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
+    if (!q) return GJ_ERR_INVALID;
+    QueryState &s = q->s;
+    DeviceGuard g(s.cs->c.device);
+    if (!s.own) {
+        std::unique_ptr<Ctx> o(new Ctx());
+        const Ctx &base = s.cs->c;
+        o->device = base.device;
+        o->pool = base.pool;
+        o->num_sms = base.num_sms;
+        if (cudaMalloc((void **)&o->err, 16) != cudaSuccess ||
+            cudaMallocHost((void **)&o->pinned, 1 << 16) != cudaSuccess) {
+            cudaGetLastError();
+            if (o->err) cudaFree(o->err);
+            return GJ_ERR_OOM;
+        }
+        cudaMemset(o->err, 0, 16);
+        // the query's earlier work (if any) ran on the context's stream
+        cudaStreamSynchronize(base.stream);
+        s.own = std::move(o);
+    } else {
+        cudaStreamSynchronize(s.own->stream);
+    }
+    s.own->stream = (cudaStream_t)cuda_stream;
+    return GJ_OK;
 }
 
 gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out) {
@@ -424,7 +467,7 @@ gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out) {
 gj_status gj_summarize(gj_query *q, uint64_t *total) {
     if (!q || !total) return GJ_ERR_INVALID;
     DeviceGuard g(q->s.cs->c.device);
-    cudaMemsetAsync(q->s.cs->c.err, 0, 4, q->s.cs->c.stream);
+    cudaMemsetAsync(q->s.ctx().err, 0, 4, q->s.ctx().stream);
     return summarize(q->s, total);
 }
 
@@ -434,7 +477,7 @@ gj_status gj_summary_groups(gj_query *q, int32_t rel, uint64_t *w_dev, uint64_t 
     if (!q->s.summarized && !q->s.overflow) return GJ_ERR_STATE;
     DeviceGuard g(q->s.cs->c.device);
     QRel &t = q->s.r[rel];
-    Ctx &c = q->s.cs->c;
+    Ctx &c = q->s.ctx();
     size_t bytes = 8 * (size_t)t.F->G;
     if (bytes) {
         if (w_dev && cudaMemcpyAsync(w_dev, t.w, bytes, cudaMemcpyDeviceToDevice, c.stream)) return GJ_ERR_CUDA;

@@ -251,7 +251,7 @@ int child_index(const QRel &parent, int child_pos) {
 // overlap result rows [row0, row_end).  keep_last: also fill lh and unit.
 cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bool keep_last,
                    Frontier &out) {
-    Ctx &c = q.cs->c;
+    Ctx &c = q.ctx();
     const QRel &root = q.r[q.pre[0]];
     uint32_t *rr = nullptr;
     GJ_CUDA_TRY(dalloc(c, &rr, 2));
@@ -499,7 +499,7 @@ __global__ void k_level_write(LevelSpec s, int64_t F, const uint8_t *flag, const
 
 gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
                       uint32_t *const *rowid_cols, uint64_t *n_out) {
-    Ctx &c = q.cs->c;
+    Ctx &c = q.ctx();
     *n_out = 0;
     if (!q.summarized) return GJ_ERR_STATE;
     if (q.overflow) return GJ_ERR_OVERFLOW;
@@ -595,7 +595,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
 
 gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, int32_t *val,
                      uint64_t *freq, uint64_t *off, uint64_t cap, uint64_t *n_out) {
-    Ctx &c = q.cs->c;
+    Ctx &c = q.ctx();
     *n_out = 0;
     if (!q.summarized) return GJ_ERR_STATE;
     if (q.overflow) return GJ_ERR_OVERFLOW;

@@ -3,6 +3,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "gj_internal.cuh"
@@ -55,6 +56,9 @@ struct Relation {
 
 struct CtxState {
     Ctx c;
+    // guards the relation and factor maps (load, release, factor builds,
+    // query planning); work on distinct queries does not take it
+    std::recursive_mutex mu;
     std::map<int32_t, std::unique_ptr<Relation>> rels;
     int32_t next_id = 1;
 };
@@ -92,6 +96,10 @@ struct QRel {
 
 struct QueryState {
     CtxState *cs = nullptr;
+    // optional execution context of this query alone (own stream, readback
+    // buffer and error word; shares the context's pool and factors)
+    std::unique_ptr<Ctx> own;
+    Ctx &ctx() { return own ? *own : cs->c; }
     int k = 0;
     std::vector<QRel> r;
     std::vector<int> pre;              // preorder of positions

@@ -286,7 +286,7 @@ void query_free_summary(Ctx &c, QueryState &q) {
 }
 
 gj_status summarize(QueryState &q, uint64_t *total_out) {
-    Ctx &c = q.cs->c;
+    Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;
 #define TRY(x)                                  \

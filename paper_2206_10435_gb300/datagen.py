@@ -249,6 +249,8 @@ def batch_queries_torch(seed: int = SEED_BASE + 3, n_queries: int = 4096,
 
     out = []
     for _ in range(n_queries):
+        if n_queries == 0:
+            break
         k = int(rng.integers(min_tables, max_tables + 1))
         rows = np.exp(rng.uniform(lo_r, hi_r, size=k)).astype(np.int64)
         doms = np.exp(rng.uniform(lo_d, hi_d, size=k + 1)).astype(np.int64)
@@ -259,3 +261,23 @@ def batch_queries_torch(seed: int = SEED_BASE + 3, n_queries: int = 4096,
             rels.append(([i, i + 1], [keys(n, s, int(doms[i])), keys(n, s, int(doms[i + 1]))]))
         out.append(rels)
     return out
+
+
+def chain_zipf_torch(seed: int, tables: int = 4, rows: int = 10**7, domain: int = 10**6,
+                     s: float = 1.1, device="cuda"):
+    """A chain R_i(K_{i-1}, K_i) with Zipf(s) keys over [0, domain), permuted
+    per (relation, column), drawn on a CUDA device; same layout as
+    batch_queries_torch (list of (attrs, [key tensors]))."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    p = torch.arange(1, domain + 1, device=device, dtype=torch.float64) ** (-s)
+    cdf = torch.cumsum(p, 0)
+    cdf /= cdf[-1].clone()
+
+    def keys():
+        u = torch.rand(rows, generator=g, device=device, dtype=torch.float64)
+        r = torch.searchsorted(cdf, u, right=True).clamp_(max=domain - 1)
+        return torch.randperm(domain, generator=g, device=device)[r].to(torch.int32)
+
+    return [([i, i + 1], [keys(), keys()]) for i in range(tables)]

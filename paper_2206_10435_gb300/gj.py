@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(_P)]),
         "gj_query_destroy": (None, [_P]),
         "gj_query_sizes": (ctypes.c_int, [_P, ctypes.POINTER(QuerySizes)]),
+        "gj_query_set_stream": (ctypes.c_int, [_P, _P]),
         "gj_summarize": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
         "gj_summary_groups": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
         "gj_level": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
@@ -254,6 +255,11 @@ class Query:
             self.close()
         except Exception:
             pass
+
+    def set_stream(self, stream):
+        """Run this query's later work on its own torch stream."""
+        _check(lib().gj_query_set_stream(self.h, _P(stream.cuda_stream)), "gj_query_set_stream")
+        self.stream = stream
 
     def summarize(self) -> int:
         """|Q|; raises GJError on overflow or failure."""
