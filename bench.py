@@ -221,6 +221,21 @@ def run_reference(a, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def reduce_over_ranks(dist, elapsed_ms: float, rows: int, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time and
+    the rows of all ranks (each rank joins its own instance, so there is no
+    data-path collective; this is the only communication).  dist is
+    torch.distributed or None; device is where the backend wants tensors."""
+    if dist is None:
+        return elapsed_ms, rows
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([rows], dtype=torch.int64, device=device)
+    dist.all_reduce(r)
+    return float(t.item()), int(r.item())
+
+
 DEFAULT_SAMPLE = {"chain5_zipf": 20000, "chain3_uniform": 10**4, "star_poisson": 10**6,
                   "batch": 0, "serve": 0}
 
@@ -312,15 +327,7 @@ def main():
             phase["summary_ms"] += ev[1].elapsed_time(ev[2]) / a.steps
             phase["desum_ms"] += ev[2].elapsed_time(ev[3]) / a.steps
     rows_local = total * a.steps
-    t_max = elapsed_ms
-    rows_all = rows_local
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        r = torch.tensor([rows_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(r)
-        rows_all = int(r.item())
+    t_max, rows_all = reduce_over_ranks(dist, elapsed_ms, rows_local, dev)
     value = rows_all / (t_max / 1000.0)
 
     # end to end through the C ABI with host buffers: H2D of the relations
