@@ -40,8 +40,10 @@ constexpr int EXP_TILE = 1024;   // output slots per CTA in expansion
 constexpr int EMIT_TILE = 1024;  // result rows per CTA in emission
 
 // One frontier: path prefixes (groups of preorder relations 0..depth-1).
+// Arrays are sized for `cap` items; the item count lives in device memory.
 struct Frontier {
-    int64_t F = 0;
+    int64_t cap = 0;
+    uint32_t *F_dev = nullptr;           // number of items
     uint64_t *A = nullptr;               // absolute first result row
     uint64_t *W = nullptr;               // product of the chosen groups' counts
     std::vector<uint32_t *> grp;         // grp[p][i]: group of preorder relation p
@@ -50,13 +52,14 @@ struct Frontier {
 };
 
 void frontier_free(Ctx &c, Frontier &f) {
+    dfree(c, f.F_dev);
     dfree(c, f.A);
     dfree(c, f.W);
     for (auto &p : f.grp) dfree(c, p);
     f.grp.clear();
     dfree(c, f.lh);
     dfree(c, f.unit);
-    f.F = 0;
+    f.cap = 0;
 }
 
 constexpr int MAXR = MAX_REL;
@@ -104,9 +107,10 @@ __device__ __forceinline__ uint32_t first_greater(uint32_t a, uint32_t b, uint64
     return a;
 }
 
-__global__ void k_expand_count(ExpandSpec s, int64_t F, uint64_t row0, uint64_t row_end,
+__global__ void k_expand_count(ExpandSpec s, const uint32_t *F_dev, uint64_t row0, uint64_t row_end,
                                uint32_t *cnt, uint32_t *lo_out, uint64_t *unit_out,
                                uint32_t *err) {
+    const int64_t F = *F_dev;
     for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
         uint32_t gp = s.grp[s.parent_p][i];
         uint32_t seg = s.link[gp];
@@ -141,68 +145,78 @@ struct ExpandOut {
 // slot_first[t] = item owning output slot t*EXP_TILE (items own the slots
 // [excl[i], excl[i] + cnt[i]) of the next frontier); one scatter pass.
 __global__ void k_slot_first(const uint32_t *__restrict__ excl, const uint32_t *__restrict__ cnt,
-                             int64_t F, int64_t tiles, uint32_t *slot_first) {
+                             const uint32_t *F_dev, uint32_t *slot_first) {
+    const int64_t F = *F_dev;
     for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
         uint64_t lo = excl[i], hi = lo + cnt[i];
-        for (uint64_t t = (lo + EXP_TILE - 1) / EXP_TILE; t * EXP_TILE < hi && (int64_t)t < tiles; t++)
+        for (uint64_t t = (lo + EXP_TILE - 1) / EXP_TILE; t * EXP_TILE < hi; t++)
             slot_first[t] = (uint32_t)i;
     }
 }
 
-// Tile of EXP_TILE output slots per CTA; slot -> source item by a search of
-// the item offsets staged in shared memory (each item has >= 1 slot).
+// Tiles of EXP_TILE output slots, taken in turn by a persistent grid (the
+// number of tiles follows from the next frontier's size in device memory);
+// slot -> source item by a search of the item offsets staged in shared
+// memory (each item has >= 1 slot).
 __global__ void __launch_bounds__(DT)
-k_expand_write(ExpandSpec s, int64_t F, const uint32_t *__restrict__ excl, int64_t Fout,
-               const uint32_t *__restrict__ slot_first, int64_t tiles,
+k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__ excl,
+               const uint32_t *Fout_dev, const uint32_t *__restrict__ slot_first,
                const uint32_t *__restrict__ lo_in, const uint64_t *__restrict__ unit_in,
                ExpandOut o) {
     __shared__ uint32_t s_off[EXP_TILE + 1];
-    const int64_t tile = blockIdx.x;
-    const int64_t o0 = tile * EXP_TILE;
-    if (o0 >= Fout) return;
-    const int64_t o1 = min((int64_t)Fout, o0 + EXP_TILE);
-    const int64_t first = slot_first[tile];
-    const int64_t last = (tile + 1 < tiles) ? (int64_t)slot_first[tile + 1] : F - 1;
-    const int nitems = (int)(last - first + 1);
-    // every item owns >= 1 slot, so a tile sees at most EXP_TILE + 1 items
-    if (last < first || nitems > EXP_TILE + 1) {
-        if (threadIdx.x == 0) raise_err(s.err, ERRF_BOUNDS);
-        return;
-    }
-    for (int t = threadIdx.x; t < nitems; t += DT) s_off[t] = excl[first + t];
-    __syncthreads();
+    const int64_t F = *F_dev, Fout = *Fout_dev;
+    const int64_t tiles = (Fout + EXP_TILE - 1) / EXP_TILE;
     const int j = s.depth;
-    for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
-        int a = 0, b = nitems;   // last t with s_off[t] <= slot
-        while (a < b) { int m = (a + b) >> 1; if (s_off[m] <= (uint32_t)slot) a = m + 1; else b = m; }
-        const int64_t i = first + a - 1;
-        const uint32_t h = lo_in[i] + (uint32_t)(slot - s_off[a - 1]);
-        const uint32_t g = s.lgid[h];
-        const uint64_t unit = unit_in[i];
-        o.A[slot] = s.A[i] + unit * s.loff[h];
-        o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
-        for (int p = 0; p < j; p++) o.grp[p][slot] = s.grp[p][i];
-        o.grp[j][slot] = g;
-        if (o.lh) o.lh[slot] = h;
-        if (o.unit) o.unit[slot] = unit;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t o0 = tile * EXP_TILE;
+        const int64_t o1 = min(Fout, o0 + EXP_TILE);
+        const int64_t first = slot_first[tile];
+        const int64_t last = (tile + 1 < tiles) ? (int64_t)slot_first[tile + 1] : F - 1;
+        const int nitems = (int)(last - first + 1);
+        // every item owns >= 1 slot, so a tile sees at most EXP_TILE + 1 items
+        if (last < first || nitems > EXP_TILE + 1) {
+            if (threadIdx.x == 0) raise_err(s.err, ERRF_BOUNDS);
+            return;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nitems; t += DT) s_off[t] = excl[first + t];
+        __syncthreads();
+        for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
+            int a = 0, b = nitems;   // last t with s_off[t] <= slot
+            while (a < b) { int m = (a + b) >> 1; if (s_off[m] <= (uint32_t)slot) a = m + 1; else b = m; }
+            const int64_t i = first + a - 1;
+            const uint32_t h = lo_in[i] + (uint32_t)(slot - s_off[a - 1]);
+            const uint32_t g = s.lgid[h];
+            const uint64_t unit = unit_in[i];
+            o.A[slot] = s.A[i] + unit * s.loff[h];
+            o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
+            for (int p = 0; p < j; p++) o.grp[p][slot] = s.grp[p][i];
+            o.grp[j][slot] = g;
+            if (o.lh) o.lh[slot] = h;
+            if (o.unit) o.unit[slot] = unit;
+        }
     }
 }
 
-__global__ void k_root_range(const uint64_t *loff, const uint64_t *lw, int64_t L, uint64_t row0,
-                             uint64_t row_end, uint32_t *out) {
+__global__ void k_root_range(const uint64_t *loff, const uint64_t *lw, const uint32_t *L_dev,
+                             uint64_t row0, uint64_t row_end, uint32_t *out, uint32_t *F_dev) {
     // live root groups h with [loff, loff + lw) overlapping [row0, row_end)
-    uint32_t a = 0, b = (uint32_t)L;
+    const uint32_t L = *L_dev;
+    uint32_t a = 0, b = L;
     while (a < b) { uint32_t m = a + ((b - a) >> 1); if (loff[m] + lw[m] > row0) b = m; else a = m + 1; }
     uint32_t lo = a;
-    a = lo; b = (uint32_t)L;
+    a = lo; b = L;
     while (a < b) { uint32_t m = a + ((b - a) >> 1); if (loff[m] > row_end - 1) b = m; else a = m + 1; }
     out[0] = lo;
     out[1] = a;
+    *F_dev = a - lo;
 }
 
-__global__ void k_root_init(uint32_t lo, int64_t F, const uint32_t *lgid, const uint64_t *loff,
-                            const uint32_t *gstart, uint64_t *A, uint64_t *W, uint32_t *grp0,
-                            uint32_t *lh, uint64_t *unit) {
+__global__ void k_root_init(const uint32_t *lo_dev, const uint32_t *F_dev, const uint32_t *lgid,
+                            const uint64_t *loff, const uint32_t *gstart, uint64_t *A, uint64_t *W,
+                            uint32_t *grp0, uint32_t *lh, uint64_t *unit) {
+    const uint32_t lo = *lo_dev;
+    const int64_t F = *F_dev;
     for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
         uint32_t h = lo + (uint32_t)i;
         uint32_t g = lgid[h];
@@ -247,33 +261,42 @@ int child_index(const QRel &parent, int child_pos) {
     return -1;
 }
 
+cudaError_t frontier_alloc(Ctx &c, Frontier &f, int64_t cap, int depth, bool keep_last) {
+    f.cap = cap;
+    GJ_CUDA_TRY(dalloc(c, &f.F_dev, 1));
+    GJ_CUDA_TRY(dalloc(c, &f.A, cap));
+    GJ_CUDA_TRY(dalloc(c, &f.W, cap));
+    f.grp.assign(depth, nullptr);
+    for (int p = 0; p < depth; p++) GJ_CUDA_TRY(dalloc(c, &f.grp[p], cap));
+    if (keep_last) {
+        GJ_CUDA_TRY(dalloc(c, &f.lh, cap));
+        GJ_CUDA_TRY(dalloc(c, &f.unit, cap));
+    }
+    return cudaSuccess;
+}
+
 // Frontier of path prefixes through preorder relations 0..depth-1 that
-// overlap result rows [row0, row_end).  keep_last: also fill lh and unit.
+// overlap result rows [row0, row_end).  No host synchronisation: every
+// frontier holds at most one item per row of the window, so arrays are
+// sized by the window and item counts stay in device memory.
+// keep_last: also fill lh and unit.
 cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bool keep_last,
                    Frontier &out) {
     Ctx &c = q.ctx();
     const QRel &root = q.r[q.pre[0]];
+    const int64_t cap = (int64_t)(row_end - row0);
+    const int pgrid = std::max(1, std::min<int>((int)ceil_div(cap, EXP_TILE), c.num_sms * 8));
     uint32_t *rr = nullptr;
     GJ_CUDA_TRY(dalloc(c, &rr, 2));
-    k_root_range<<<1, 1, 0, c.stream>>>(root.loff, root.lw, root.L, row0, row_end, rr); c.launches++;
-    uint32_t hr[2];
-    GJ_CUDA_TRY(readback(c, rr, hr, 8));
-    dfree(c, rr);
     Frontier cur;
-    cur.F = (int64_t)hr[1] - hr[0];
-    bool last = depth == 1;
-    GJ_CUDA_TRY(dalloc(c, &cur.A, cur.F));
-    GJ_CUDA_TRY(dalloc(c, &cur.W, cur.F));
-    cur.grp.assign(1, nullptr);
-    GJ_CUDA_TRY(dalloc(c, &cur.grp[0], cur.F));
-    if (last && keep_last) {
-        GJ_CUDA_TRY(dalloc(c, &cur.lh, cur.F));
-        GJ_CUDA_TRY(dalloc(c, &cur.unit, cur.F));
-    }
-    k_root_init<<<grid_for(c, cur.F), DT, 0, c.stream>>>(hr[0], cur.F, root.lgid, root.loff,
-                                                        root.F->gstart, cur.A, cur.W, cur.grp[0],
-                                                        cur.lh, cur.unit); c.launches++;
+    GJ_CUDA_TRY(frontier_alloc(c, cur, cap, 1, keep_last && depth == 1));
+    k_root_range<<<1, 1, 0, c.stream>>>(root.loff, root.lw, root.L_dev, row0, row_end, rr,
+                                        cur.F_dev); c.launches++;
+    k_root_init<<<grid_for(c, cap), DT, 0, c.stream>>>(rr, cur.F_dev, root.lgid, root.loff,
+                                                      root.F->gstart, cur.A, cur.W, cur.grp[0],
+                                                      cur.lh, cur.unit); c.launches++;
     GJ_CUDA_TRY(cudaGetLastError());
+    dfree(c, rr);
     for (int j = 1; j < depth; j++) {
         const int tpos = q.pre[j];
         const QRel &t = q.r[tpos];
@@ -301,51 +324,35 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         s.A = cur.A;
         s.W = cur.W;
         for (int p = 0; p < j; p++) s.grp[p] = cur.grp[p];
-        uint32_t *cnt = nullptr, *lo = nullptr, *excl = nullptr, *tot = nullptr;
+        uint32_t *cnt = nullptr, *lo = nullptr, *excl = nullptr, *slot_first = nullptr;
         uint64_t *unit = nullptr;
-        GJ_CUDA_TRY(dalloc(c, &cnt, cur.F));
-        GJ_CUDA_TRY(dalloc(c, &lo, cur.F));
-        GJ_CUDA_TRY(dalloc(c, &unit, cur.F));
-        GJ_CUDA_TRY(dalloc(c, &excl, cur.F));
-        GJ_CUDA_TRY(dalloc(c, &tot, 1));
-        k_expand_count<<<grid_for(c, cur.F), DT, 0, c.stream>>>(s, cur.F, row0, row_end, cnt, lo,
-                                                              unit, c.err); c.launches++;
-        GJ_CUDA_TRY(cudaGetLastError());
-        GJ_CUDA_TRY(scan_u32(c, cnt, nullptr, excl, cur.F, tot));
-        uint32_t Fn = 0;
-        GJ_CUDA_TRY(readback(c, tot, &Fn, 4));
+        GJ_CUDA_TRY(dalloc(c, &cnt, cap));
+        GJ_CUDA_TRY(dalloc(c, &lo, cap));
+        GJ_CUDA_TRY(dalloc(c, &unit, cap));
+        GJ_CUDA_TRY(dalloc(c, &excl, cap));
+        GJ_CUDA_TRY(dalloc(c, &slot_first, ceil_div(cap, EXP_TILE) + 1));
+        const bool last = (j == depth - 1);
         Frontier nxt;
-        nxt.F = Fn;
-        GJ_CUDA_TRY(dalloc(c, &nxt.A, nxt.F));
-        GJ_CUDA_TRY(dalloc(c, &nxt.W, nxt.F));
-        nxt.grp.assign(j + 1, nullptr);
-        for (int p = 0; p <= j; p++) GJ_CUDA_TRY(dalloc(c, &nxt.grp[p], nxt.F));
-        last = (j == depth - 1);
-        if (last && keep_last) {
-            GJ_CUDA_TRY(dalloc(c, &nxt.lh, nxt.F));
-            GJ_CUDA_TRY(dalloc(c, &nxt.unit, nxt.F));
-        }
+        GJ_CUDA_TRY(frontier_alloc(c, nxt, cap, j + 1, last && keep_last));
+        k_expand_count<<<grid_for(c, cap), DT, 0, c.stream>>>(s, cur.F_dev, row0, row_end, cnt, lo,
+                                                            unit, c.err); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        GJ_CUDA_TRY(scan_u32_dev(c, cnt, nullptr, excl, cap, cur.F_dev, nxt.F_dev));
         ExpandOut o{};
         o.A = nxt.A;
         o.W = nxt.W;
         for (int p = 0; p <= j; p++) o.grp[p] = nxt.grp[p];
         o.lh = nxt.lh;
         o.unit = nxt.unit;
-        if (nxt.F > 0) {
-            const int64_t tiles = ceil_div(nxt.F, EXP_TILE);
-            uint32_t *slot_first = nullptr;
-            GJ_CUDA_TRY(dalloc(c, &slot_first, tiles + 1));
-            k_slot_first<<<grid_for(c, cur.F), DT, 0, c.stream>>>(excl, cnt, cur.F, tiles, slot_first); c.launches++;
-            k_expand_write<<<(unsigned)tiles, DT, 0, c.stream>>>(
-                s, cur.F, excl, nxt.F, slot_first, tiles, lo, unit, o); c.launches++;
-            GJ_CUDA_TRY(cudaGetLastError());
-            dfree(c, slot_first);
-        }
+        k_slot_first<<<grid_for(c, cap), DT, 0, c.stream>>>(excl, cnt, cur.F_dev, slot_first); c.launches++;
+        k_expand_write<<<pgrid, DT, 0, c.stream>>>(s, cur.F_dev, excl, nxt.F_dev, slot_first, lo,
+                                                   unit, o); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
         dfree(c, cnt);
         dfree(c, lo);
         dfree(c, unit);
         dfree(c, excl);
-        dfree(c, tot);
+        dfree(c, slot_first);
         frontier_free(c, cur);
         cur = nxt;
     }
@@ -379,7 +386,8 @@ struct EmitSpec {
 };
 
 __global__ void __launch_bounds__(DT)
-k_emit(EmitSpec e, int64_t B, uint64_t row0, int64_t n) {
+k_emit(EmitSpec e, const uint32_t *B_dev, uint64_t row0, int64_t n) {
+    const int64_t B = *B_dev;
     __shared__ uint64_t s_A[EMIT_TILE + 1];
     __shared__ int64_t s_first;
     __shared__ int s_cnt;
@@ -446,7 +454,7 @@ struct LevelSpec {
     const uint64_t *loff, *lw;
     const uint32_t *seg_id;       // NULL for the root
     const uint32_t *lseg_first;
-    int64_t L;
+    const uint32_t *L_dev;
     int nprefix;                  // new columns up to and including the level's
     bool last;                    // level's column is the relation's last new column
     const int32_t *pcol[MAX_KEYS];
@@ -459,7 +467,8 @@ __device__ __forceinline__ bool same_prefix(const LevelSpec &s, uint32_t g1, uin
     return true;
 }
 
-__global__ void k_level_flags(LevelSpec s, int64_t F, uint64_t row0, uint8_t *flag) {
+__global__ void k_level_flags(LevelSpec s, const uint32_t *F_dev, uint64_t row0, uint8_t *flag) {
+    const int64_t F = *F_dev;
     for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
         uint8_t f = 0;
         if (s.A[i] >= row0) {
@@ -472,15 +481,16 @@ __global__ void k_level_flags(LevelSpec s, int64_t F, uint64_t row0, uint8_t *fl
     }
 }
 
-__global__ void k_level_write(LevelSpec s, int64_t F, const uint8_t *flag, const uint32_t *idx,
-                              int32_t *val, uint64_t *freq, uint64_t *off) {
+__global__ void k_level_write(LevelSpec s, const uint32_t *F_dev, const uint8_t *flag,
+                              const uint32_t *idx, int32_t *val, uint64_t *freq, uint64_t *off) {
+    const int64_t F = *F_dev;
     for (int64_t i = (int64_t)blockIdx.x * DT + threadIdx.x; i < F; i += (int64_t)gridDim.x * DT) {
         if (!flag[i]) continue;
         uint32_t h = s.lh[i];
         uint32_t g = s.lgid[h];
         uint32_t he = h;
         if (!s.last) {
-            uint32_t b = s.seg_id ? s.lseg_first[s.seg_id[g] + 1] : (uint32_t)s.L;
+            uint32_t b = s.seg_id ? s.lseg_first[s.seg_id[g] + 1] : *s.L_dev;
             uint32_t a = h + 1;   // first live index after h with a different prefix
             while (a < b) {
                 uint32_t m = a + ((b - a) >> 1);
@@ -544,11 +554,12 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
             }
         }
         s.col_off[q.k] = nc;
-        for (int i = 0; i < nc; i++) vec &= ((uintptr_t)s.dst[i] & 15) == 0;
+        // 32-byte vector stores need 32-byte aligned columns
+        for (int i = 0; i < nc; i++) vec &= ((uintptr_t)s.dst[i] & 31) == 0;
         s.vec = vec;
         s.A = f.A;
         s.err = c.err;
-        e = launch_emit(c, q.k, s, f.F, row0, (int64_t)n);
+        e = launch_emit(c, q.k, s, f.F_dev, row0, (int64_t)n);
     } else {
         EmitSpec s{};
         s.k = q.k;
@@ -576,7 +587,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
         }
         s.A = f.A;
         s.err = c.err;
-        k_emit<<<(unsigned)ceil_div((int64_t)n, EMIT_TILE), DT, 0, c.stream>>>(s, f.F, row0, (int64_t)n); c.launches++;
+        k_emit<<<(unsigned)ceil_div((int64_t)n, EMIT_TILE), DT, 0, c.stream>>>(s, f.F_dev, row0, (int64_t)n); c.launches++;
         e = cudaGetLastError();
     }
     if (c.prof) {
@@ -618,7 +629,7 @@ gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, in
     s.lw = t.lw;
     s.seg_id = t.parent >= 0 ? t.seg_id : nullptr;
     s.lseg_first = t.lseg_first;
-    s.L = t.L;
+    s.L_dev = t.L_dev;
     int m = -1;
     for (size_t i = 0; i < t.new_cols.size(); i++)
         if (t.new_cols[i] == q.var_col[level]) m = (int)i;
@@ -630,15 +641,15 @@ gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, in
     uint32_t *idx = nullptr, *tot = nullptr;
     gj_status st = GJ_OK;
     uint32_t R = 0;
-    if ((e = dalloc(c, &flag, f.F)) != cudaSuccess) goto fail;
-    if ((e = dalloc(c, &idx, f.F)) != cudaSuccess) goto fail;
+    if ((e = dalloc(c, &flag, f.cap)) != cudaSuccess) goto fail;
+    if ((e = dalloc(c, &idx, f.cap)) != cudaSuccess) goto fail;
     if ((e = dalloc(c, &tot, 1)) != cudaSuccess) goto fail;
-    k_level_flags<<<grid_for(c, f.F), DT, 0, c.stream>>>(s, f.F, row0, flag); c.launches++;
-    if ((e = scan_u32(c, nullptr, flag, idx, f.F, tot)) != cudaSuccess) goto fail;
+    k_level_flags<<<grid_for(c, f.cap), DT, 0, c.stream>>>(s, f.F_dev, row0, flag); c.launches++;
+    if ((e = scan_u32_dev(c, nullptr, flag, idx, f.cap, f.F_dev, tot)) != cudaSuccess) goto fail;
     if ((e = readback(c, tot, &R, 4)) != cudaSuccess) goto fail;
     *n_out = R;
     if (R > cap) { st = GJ_ERR_CAPACITY; goto done; }
-    k_level_write<<<grid_for(c, f.F), DT, 0, c.stream>>>(s, f.F, flag, idx, val, freq, off); c.launches++;
+    k_level_write<<<grid_for(c, f.cap), DT, 0, c.stream>>>(s, f.F_dev, flag, idx, val, freq, off); c.launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) goto fail;
     st = check_device_error(c);
     goto done;

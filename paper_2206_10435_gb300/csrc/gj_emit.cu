@@ -20,8 +20,9 @@ namespace {
 
 // tile_first[t] = block holding the first row of emit tile t (rows
 // [row0 + t*T, ...)); written by the blocks themselves, one scatter pass.
-__global__ void k_tile_first(const uint64_t *__restrict__ A, int64_t B, uint64_t row0, int64_t n,
-                             int64_t tiles, uint32_t *tile_first) {
+__global__ void k_tile_first(const uint64_t *__restrict__ A, const uint32_t *B_dev, uint64_t row0,
+                             int64_t n, int64_t tiles, uint32_t *tile_first) {
+    const int64_t B = *B_dev;
     for (int64_t b = (int64_t)blockIdx.x * EMIT_DT + threadIdx.x; b < B; b += (int64_t)gridDim.x * EMIT_DT) {
         uint64_t lo = A[b] > row0 ? A[b] - row0 : 0;
         uint64_t hi = (b + 1 < B) ? A[b + 1] - row0 : (uint64_t)n;
@@ -31,49 +32,58 @@ __global__ void k_tile_first(const uint64_t *__restrict__ A, int64_t B, uint64_t
     }
 }
 
-// Writes one column of the warp's 128 rows (4 per lane, consecutive):
-// the values go through the warp's shared-memory slot and come back
-// transposed, so each store instruction covers 32 consecutive rows.
-// 32-bit values: one 16-byte shared store per lane (conflict-free); 64-bit
-// values: lane-major with one pad word per lane, so the 8-byte stores of a
-// half-warp hit distinct banks.
-__device__ __forceinline__ void emit_store_col(unsigned int *slot, const unsigned int (&v)[EMIT_RPT],
-                                               unsigned int *dst, int64_t wrow0, int64_t r1,
-                                               int lane) {
-    __syncwarp();
-    *(uint4 *)(slot + lane * EMIT_RPT) = make_uint4(v[0], v[1], v[2], v[3]);
-    __syncwarp();
+// Column stores.  A lane holds 4 consecutive rows of a column.  Every store
+// writes whole 32-byte sectors: a 64-bit column stores its 4 values as one
+// 32-byte vector store; a 32-bit column pairs lanes (2m, 2m+1) by shuffle
+// and lane 2m stores the pair's 8 consecutive values as one 32-byte vector
+// store.  Edges of the window (or unaligned buffers) fall back to scalar
+// stores.  Streaming (.cs) stores: the result is not read back here.
+__device__ __forceinline__ void st_cs_v4_b64(unsigned long long *p, const unsigned long long (&v)[EMIT_RPT]) {
+    asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(v[0]), "l"(v[1]),
+                 "l"(v[2]), "l"(v[3]) : "memory");
+}
+
+__device__ __forceinline__ void st_cs_v8_b32(unsigned int *p, const unsigned int (&a)[EMIT_RPT],
+                                             const unsigned int (&b)[EMIT_RPT]) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
+                 "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
+                 "r"(b[3]) : "memory");
+}
+
+__device__ __forceinline__ void emit_store_col(const unsigned long long (&v)[EMIT_RPT],
+                                               unsigned long long *dst, int64_t rbeg, int nrow,
+                                               bool vec) {
+    if (vec && nrow == EMIT_RPT) {
+        st_cs_v4_b64(dst + rbeg, v);
+    } else {
 #pragma unroll
-    for (int m = 0; m < EMIT_RPT; m++) {
-        int64_t r = wrow0 + m * 32 + lane;
-        if (r < r1) __stcs(dst + r, slot[m * 32 + lane]);
+        for (int i = 0; i < EMIT_RPT; i++)
+            if (i < nrow) __stcs(dst + rbeg + i, v[i]);
     }
 }
 
-constexpr int SLOT64_STRIDE = EMIT_RPT + 1;
-
-__device__ __forceinline__ void emit_store_col(unsigned long long *slot,
-                                               const unsigned long long (&v)[EMIT_RPT],
-                                               unsigned long long *dst, int64_t wrow0, int64_t r1,
+// all lanes of the warp must call this (shuffles)
+__device__ __forceinline__ void emit_store_col(const unsigned int (&v)[EMIT_RPT], unsigned int *dst,
+                                               int64_t rbeg, int nrow, int pair_rows, bool vec,
                                                int lane) {
-    __syncwarp();
+    unsigned int o[EMIT_RPT];
 #pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++) slot[lane * SLOT64_STRIDE + i] = v[i];
-    __syncwarp();
+    for (int i = 0; i < EMIT_RPT; i++) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
+    if (vec && pair_rows == 2 * EMIT_RPT) {
+        if ((lane & 1) == 0) st_cs_v8_b32(dst + rbeg, v, o);
+    } else {
 #pragma unroll
-    for (int m = 0; m < EMIT_RPT; m++) {
-        int q = m * 32 + lane;
-        int64_t r = wrow0 + q;
-        if (r < r1) __stcs(dst + r, slot[(q >> 2) * SLOT64_STRIDE + (q & 3)]);
+        for (int i = 0; i < EMIT_RPT; i++)
+            if (i < nrow) __stcs(dst + rbeg + i, v[i]);
     }
 }
 
 template <int K>
-__global__ void __launch_bounds__(EMIT_DT)
-k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int64_t B,
+__global__ void __launch_bounds__(EMIT_DT, (K <= 5 ? 4 : 3))
+k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, const uint32_t *B_dev,
         uint64_t row0, int64_t n) {
+    const int64_t B = *B_dev;
     __shared__ uint64_t s_A[EMIT4_TILE + 1];
-    __shared__ __align__(16) unsigned long long s_stage[EMIT_DT / 32][32 * SLOT64_STRIDE];
     const int64_t tile = blockIdx.x;
     const int64_t r0 = tile * EMIT4_TILE;
     if (r0 >= n) return;
@@ -88,11 +98,12 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int
     }
     for (int t = threadIdx.x; t < nb; t += EMIT_DT) s_A[t] = e.A[first + t];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t wrow0 = r0 + (int64_t)warp * 32 * EMIT_RPT;
+    const int lane = threadIdx.x & 31;
     const int64_t rbeg = r0 + (int64_t)threadIdx.x * EMIT_RPT;
-    // lanes past the end still take part in the warp's transposes
+    // lanes past the end still take part in the warp's shuffles
     const int nrow = (int)max((int64_t)0, min((int64_t)EMIT_RPT, r1 - rbeg));
+    // rows of the lane pair (2m, 2m+1) that lane 2m would store
+    const int pair_rows = (int)max((int64_t)0, min((int64_t)2 * EMIT_RPT, r1 - (rbeg & ~(int64_t)(2 * EMIT_RPT - 1))));
     const uint64_t row = row0 + (uint64_t)rbeg;
     // block of every row: a search for the first, then at most one step per row
     int lb[EMIT_RPT];
@@ -109,14 +120,18 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int
         if (i < nrow && lb[i] + 1 < nb && s_A[lb[i] + 1] <= row + i) lb[i]++;
     }
     const uint64_t q0 = nrow > 0 ? row - s_A[lb[0]] : 0;
-    unsigned int *slot32 = (unsigned int *)s_stage[warp];
-    unsigned long long *slot64 = s_stage[warp];
-    // all group ids, then all group extents: two rounds of independent loads
+    // all group ids, then all group extents: two rounds of independent loads;
+    // a row in the same block as the previous row reuses its values (the
+    // load is predicated off, so it costs no memory traffic)
+    bool nb_row[EMIT_RPT];
+#pragma unroll
+    for (int i = 0; i < EMIT_RPT; i++) nb_row[i] = (i == 0) || lb[i] != lb[i - 1];
     uint32_t g[EMIT_RPT][K];
 #pragma unroll
     for (int i = 0; i < EMIT_RPT; i++)
 #pragma unroll
-        for (int j = 0; j < K; j++) g[i][j] = __ldg(e.grp[j] + first + lb[i]);
+        for (int j = 0; j < K; j++)
+            g[i][j] = nb_row[i] ? __ldg(e.grp[j] + first + lb[i]) : g[i > 0 ? i - 1 : 0][j];
     // key columns need only the groups: write them while extents load
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -125,8 +140,9 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int
             const unsigned int *src = (const unsigned int *)e.src[c];
             unsigned int v[EMIT_RPT];
 #pragma unroll
-            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + g[i][j]);
-            emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
+            for (int i = 0; i < EMIT_RPT; i++)
+                v[i] = nb_row[i] ? __ldg(src + g[i][j]) : v[i > 0 ? i - 1 : 0];
+            emit_store_col(v, (unsigned int *)e.dst[c], rbeg, nrow, pair_rows, e.vec, lane);
         }
     }
     uint32_t pos[EMIT_RPT][K];
@@ -136,8 +152,13 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int
         for (int i = 0; i < EMIT_RPT; i++)
 #pragma unroll
             for (int j = 0; j < K; j++) {
-                base[i][j] = __ldg(e.gstart[j] + g[i][j]);
-                cnt[i][j] = __ldg(e.gstart[j] + g[i][j] + 1) - base[i][j];
+                if (nb_row[i]) {
+                    base[i][j] = __ldg(e.gstart[j] + g[i][j]);
+                    cnt[i][j] = __ldg(e.gstart[j] + g[i][j] + 1) - base[i][j];
+                } else {
+                    base[i][j] = base[i > 0 ? i - 1 : 0][j];
+                    cnt[i][j] = cnt[i > 0 ? i - 1 : 0][j];
+                }
             }
         // digits of the first row (relation k-1 fastest), then an odometer
         uint32_t d[K];
@@ -186,34 +207,35 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, int
                 unsigned long long v[EMIT_RPT];
 #pragma unroll
                 for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(slot64, v, (unsigned long long *)e.dst[c],
-                                                   wrow0, r1, lane);
+                emit_store_col(v, (unsigned long long *)e.dst[c], rbeg, nrow, e.vec);
             } else if (kind == 1) {
                 const unsigned int *src = (const unsigned int *)e.src[c];
                 unsigned int v[EMIT_RPT];
 #pragma unroll
                 for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(slot32, v, (unsigned int *)e.dst[c], wrow0, r1, lane);
+                emit_store_col(v, (unsigned int *)e.dst[c], rbeg, nrow, pair_rows, e.vec, lane);
             }
         }
         if (e.rid_out[j]) {
             unsigned int v[EMIT_RPT];
 #pragma unroll
             for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
-            emit_store_col(slot32, v, e.rid_out[j], wrow0, r1, lane);
+            emit_store_col(v, e.rid_out[j], rbeg, nrow, pair_rows,
+                           e.vec && ((uintptr_t)e.rid_out[j] & 31) == 0, lane);
         }
     }
 }
 
 template <int K>
-cudaError_t launch_k(Ctx &c, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n) {
+cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0, int64_t n) {
     const int64_t tiles = ceil_div(n, EMIT4_TILE);
     uint32_t *tile_first = nullptr;
     GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(B, EMIT_DT), (int64_t)c.num_sms * 16));
-    k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B, row0, n, tiles, tile_first); c.launches++;
+    // at most one block per row of the window
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, EMIT_DT), (int64_t)c.num_sms * 16));
+    k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, tile_first); c.launches++;
     if (c.prof) cudaEventRecord(c.event(), c.stream);
-    k_emit4<K><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, tile_first, tiles, B, row0, n); c.launches++;
+    k_emit4<K><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, tile_first, tiles, B_dev, row0, n); c.launches++;
     cudaError_t e = cudaGetLastError();
     dfree(c, tile_first);
     return e;
@@ -221,16 +243,17 @@ cudaError_t launch_k(Ctx &c, const Emit4Spec &s, int64_t B, uint64_t row0, int64
 
 }  // namespace
 
-cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n) {
+cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
+                        int64_t n) {
     switch (k) {
-        case 1: return launch_k<1>(c, s, B, row0, n);
-        case 2: return launch_k<2>(c, s, B, row0, n);
-        case 3: return launch_k<3>(c, s, B, row0, n);
-        case 4: return launch_k<4>(c, s, B, row0, n);
-        case 5: return launch_k<5>(c, s, B, row0, n);
-        case 6: return launch_k<6>(c, s, B, row0, n);
-        case 7: return launch_k<7>(c, s, B, row0, n);
-        case 8: return launch_k<8>(c, s, B, row0, n);
+        case 1: return launch_k<1>(c, s, B_dev, row0, n);
+        case 2: return launch_k<2>(c, s, B_dev, row0, n);
+        case 3: return launch_k<3>(c, s, B_dev, row0, n);
+        case 4: return launch_k<4>(c, s, B_dev, row0, n);
+        case 5: return launch_k<5>(c, s, B_dev, row0, n);
+        case 6: return launch_k<6>(c, s, B_dev, row0, n);
+        case 7: return launch_k<7>(c, s, B_dev, row0, n);
+        case 8: return launch_k<8>(c, s, B_dev, row0, n);
     }
     return cudaErrorInvalidValue;
 }

@@ -28,8 +28,10 @@ struct Emit4Spec {
 };
 
 
-// Emits result rows [row0, row0 + n) from the block list A (B blocks): a
+// Emits result rows [row0, row0 + n) from the block list A: a
 // tile-to-block scatter, then the emit kernel for K = k relations (k <= 8).
-cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, int64_t B, uint64_t row0, int64_t n);
+// B_dev: number of blocks, in device memory.
+cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
+                        int64_t n);
 
 }  // namespace gj

@@ -99,6 +99,11 @@ inline void dfree(Ctx &c, T *&p) {
 cudaError_t scan_u32(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
                      int64_t n, uint32_t *total_dev);
 
+// scan_u32 over the first *n_dev elements (a count in device memory) of
+// arrays sized for `cap`; *total_dev may alias nothing else.  No host sync.
+cudaError_t scan_u32_dev(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
+                         int64_t cap, const uint32_t *n_dev, uint32_t *total_dev);
+
 // saturating u64, optionally segmented: heads[i] != 0 starts a new segment
 // (the exclusive value there is 0).  seg_total[s] (if non-NULL) receives the
 // saturating sum of segment s, with seg_id[i] mapping element i to its

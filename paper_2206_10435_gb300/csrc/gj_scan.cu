@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
        const uint8_t *__restrict__ heads, T *__restrict__ out, int64_t n,
        uint32_t *tile_counter, uint32_t *st_flag, T *st_agg, T *st_inc, T *total,
-       T *seg_total, const uint32_t *__restrict__ seg_id, uint32_t *err) {
+       T *seg_total, const uint32_t *__restrict__ seg_id, uint32_t *err,
+       const uint32_t *n_dev) {
     constexpr int TILE = SCAN_THREADS * ITEMS;
     __shared__ T s_val[TILE];
     __shared__ uint8_t s_head[SEG ? TILE : 1];
@@ -51,6 +52,16 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
     __syncthreads();
     const uint32_t tile = s_tile;
     const int64_t base = (int64_t)tile * TILE;
+    // element count held in device memory (grid sized for a capacity):
+    // tiles past it leave at once; none of the needed tiles waits on them
+    if (n_dev) {
+        n = min(n, (int64_t)*n_dev);
+        if (n == 0) {
+            if (tile == 0 && tid == 0 && total) *total = T(0);
+            return;
+        }
+        if (base >= n) return;
+    }
 
     // coalesced load into shared memory
 #pragma unroll
@@ -169,7 +180,8 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
 
 template <class T, class Op, int ITEMS, bool SEG>
 cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *heads, T *out,
-                        int64_t n, T *total, T *seg_total, const uint32_t *seg_id) {
+                        int64_t n, T *total, T *seg_total, const uint32_t *seg_id,
+                        const uint32_t *n_dev = nullptr) {
     constexpr int TILE = SCAN_THREADS * ITEMS;
     if (n <= 0) {
         if (total) GJ_CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(T), c.stream));
@@ -188,7 +200,7 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
     T *agg = (T *)((char *)state + 16 + flag_bytes);
     T *inc = agg + tiles;
     k_scan<T, Op, ITEMS, SEG><<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(
-        in, fv, heads, out, n, counter, flags, agg, inc, total, seg_total, seg_id, c.err); c.launches++;
+        in, fv, heads, out, n, counter, flags, agg, inc, total, seg_total, seg_id, c.err, n_dev); c.launches++;
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(state, c.stream);
     return e;
@@ -210,6 +222,16 @@ cudaError_t scan_u64_sat(Ctx &c, const uint64_t *in, const uint8_t *heads, uint6
                                                          total_dev, seg_total, seg_id);
     return launch_scan<uint64_t, SatAddU64, 8, false>(c, in, nullptr, nullptr, out, n,
                                                       total_dev, nullptr, nullptr);
+}
+
+cudaError_t scan_u32_dev(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
+                         int64_t cap, const uint32_t *n_dev, uint32_t *total_dev) {
+    if (cap <= 0) {
+        if (total_dev) GJ_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), c.stream));
+        return cudaSuccess;
+    }
+    return launch_scan<uint32_t, AddU32, 16, false>(c, in, flags, nullptr, out, cap, total_dev,
+                                                    nullptr, nullptr, n_dev);
 }
 
 }  // namespace gj
@@ -241,7 +263,8 @@ cudaError_t scan_u32_in(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32
     uint32_t *agg = (uint32_t *)((char *)state + 16 + flag_bytes);
     uint32_t *inc = agg + tiles;
     k_scan<uint32_t, AddU32, 16, false><<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(
-        in, flags, nullptr, out, n, counter, fl, agg, inc, total_dev, nullptr, nullptr, c.err); c.launches++;
+        in, flags, nullptr, out, n, counter, fl, agg, inc, total_dev, nullptr, nullptr, c.err,
+        nullptr); c.launches++;
     return cudaGetLastError();
 }
 

@@ -74,8 +74,9 @@ struct QRel {
     std::vector<int> sep_cols;         // separator columns in this relation
     std::vector<int> sep_cols_parent;  // matching columns in the parent
     std::vector<int> new_cols;         // columns whose attribute the parent lacks
-    // segments over the separator (non-root)
-    int64_t S = 0;
+    // segments over the separator (non-root); their number S lives in
+    // device memory (*S_dev), arrays are sized for G >= S
+    uint32_t *S_dev = nullptr;
     uint32_t *seg_id = nullptr;        // [G]
     uint32_t *seg_first = nullptr;     // [S+1]
     // link to each child's segments: link[i][g] for children[i]
@@ -86,8 +87,8 @@ struct QRel {
     uint64_t *msg = nullptr;           // [S] (non-root)
     uint64_t *down = nullptr;          // [S] (non-root)
     uint64_t *mult = nullptr;          // [G]
-    // live (w > 0) groups, in group order
-    int64_t L = 0;
+    // live (w > 0) groups, in group order; their number L is *L_dev
+    uint32_t *L_dev = nullptr;
     uint32_t *lgid = nullptr;          // [L]
     uint64_t *loff = nullptr;          // [L]
     uint64_t *lw = nullptr;            // [L]

@@ -31,6 +31,9 @@
 #include "gj_state.cuh"
 
 namespace gj {
+
+void note_cuda_error(cudaError_t e, const char *file, int line);
+
 namespace {
 
 constexpr int ST = 256;
@@ -67,22 +70,23 @@ __global__ void k_seg_heads(KeyCols sep, int64_t G, uint8_t *heads) {
     }
 }
 
-__global__ void k_seg_finalize(const uint8_t *heads, const uint32_t *excl, int64_t G, int64_t S,
-                               uint32_t *seg_id, uint32_t *seg_first) {
+__global__ void k_seg_finalize(const uint8_t *heads, const uint32_t *excl, int64_t G,
+                               const uint32_t *S_dev, uint32_t *seg_id, uint32_t *seg_first) {
     GRID_LOOP(g, G) {
         uint32_t s = excl[g] + heads[g] - 1u;
         seg_id[g] = s;
         if (heads[g]) seg_first[s] = (uint32_t)g;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) seg_first[S] = (uint32_t)G;
+    if (blockIdx.x == 0 && threadIdx.x == 0) seg_first[*S_dev] = (uint32_t)G;
 }
 
 __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
     GRID_LOOP(i, n) p[i] = v;
 }
 
-__global__ void k_dense_fill(const int32_t *child_key, const uint32_t *seg_first, int64_t S,
-                             int32_t mn, uint32_t *dense) {
+__global__ void k_dense_fill(const int32_t *child_key, const uint32_t *seg_first,
+                             const uint32_t *S_dev, int32_t mn, uint32_t *dense) {
+    const int64_t S = *S_dev;
     GRID_LOOP(s, S) dense[(uint32_t)child_key[seg_first[s]] - (uint32_t)mn] = (uint32_t)s;
 }
 
@@ -95,7 +99,8 @@ __global__ void k_link_dense(const int32_t *parent_key, int64_t Gp, int32_t mn, 
 }
 
 __global__ void k_link_search(KeyCols pk, int64_t Gp, KeyCols ck, const uint32_t *seg_first,
-                              int64_t S, uint32_t *link) {
+                              const uint32_t *S_dev, uint32_t *link) {
+    const int64_t S = *S_dev;
     GRID_LOOP(g, Gp) {
         int32_t want[MAX_KEYS];
         for (int c = 0; c < pk.ncol; c++) want[c] = pk.col[c][g];
@@ -158,8 +163,9 @@ __global__ void k_down_contrib(const uint32_t *gstart, int64_t G, const uint64_t
     }
 }
 
-__global__ void k_down_finalize(const unsigned long long *lo, const unsigned int *carry, int64_t S,
-                                uint64_t *down) {
+__global__ void k_down_finalize(const unsigned long long *lo, const unsigned int *carry,
+                                const uint32_t *S_dev, uint64_t *down) {
+    const int64_t S = *S_dev;
     GRID_LOOP(s, S) down[s] = (carry[s] || lo[s] == SAT) ? SAT : (uint64_t)lo[s];
 }
 
@@ -184,10 +190,11 @@ __global__ void k_live_compact(const uint8_t *f, const uint32_t *lidx, const uin
     }
 }
 
-__global__ void k_live_segs(const uint32_t *seg_first, const uint32_t *lidx, int64_t S, int64_t L,
-                            uint32_t *lseg_first) {
+__global__ void k_live_segs(const uint32_t *seg_first, const uint32_t *lidx,
+                            const uint32_t *S_dev, const uint32_t *L_dev, uint32_t *lseg_first) {
+    const int64_t S = *S_dev;
     GRID_LOOP(s, S) lseg_first[s] = lidx[seg_first[s]];
-    if (blockIdx.x == 0 && threadIdx.x == 0) lseg_first[S] = (uint32_t)L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) lseg_first[S] = *L_dev;
 }
 
 inline KeyCols key_cols(const QRel &q, const std::vector<int> &cols) {
@@ -197,33 +204,21 @@ inline KeyCols key_cols(const QRel &q, const std::vector<int> &cols) {
     return k;
 }
 
-cudaError_t readback_u32(Ctx &c, const uint32_t *dev, uint32_t *out) {
-    uint32_t *h = (uint32_t *)c.pinned;
-    GJ_CUDA_TRY(cudaMemcpyAsync(h, dev, 4, cudaMemcpyDeviceToHost, c.stream));
-    GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    *out = h[0];
-    return cudaSuccess;
-}
-
 cudaError_t build_segments(Ctx &c, QRel &t) {
     const int64_t G = t.F->G;
     GJ_CUDA_TRY(dalloc(c, &t.seg_id, G));
+    GJ_CUDA_TRY(dalloc(c, &t.seg_first, G + 1));
+    GJ_CUDA_TRY(dalloc(c, &t.S_dev, 1));
     uint8_t *heads = nullptr;
-    uint32_t *excl = nullptr, *cnt = nullptr;
+    uint32_t *excl = nullptr;
     GJ_CUDA_TRY(dalloc(c, &heads, G));
     GJ_CUDA_TRY(dalloc(c, &excl, G));
-    GJ_CUDA_TRY(dalloc(c, &cnt, 1));
     k_seg_heads<<<grid_for(c, G), ST, 0, c.stream>>>(key_cols(t, t.sep_cols), G, heads); c.launches++;
-    GJ_CUDA_TRY(scan_u32(c, nullptr, heads, excl, G, cnt));
-    uint32_t S = 0;
-    GJ_CUDA_TRY(readback_u32(c, cnt, &S));
-    t.S = S;
-    GJ_CUDA_TRY(dalloc(c, &t.seg_first, t.S + 1));
-    k_seg_finalize<<<grid_for(c, G), ST, 0, c.stream>>>(heads, excl, G, t.S, t.seg_id, t.seg_first); c.launches++;
+    GJ_CUDA_TRY(scan_u32(c, nullptr, heads, excl, G, t.S_dev));
+    k_seg_finalize<<<grid_for(c, G), ST, 0, c.stream>>>(heads, excl, G, t.S_dev, t.seg_id, t.seg_first); c.launches++;
     GJ_CUDA_TRY(cudaGetLastError());
     dfree(c, heads);
     dfree(c, excl);
-    dfree(c, cnt);
     return cudaSuccess;
 }
 
@@ -235,7 +230,7 @@ cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
     GJ_CUDA_TRY(dalloc(c, &link, Gp));
     *link_out = link;
     if (Gp == 0) return cudaSuccess;
-    if (ch.S == 0) {
+    if (ch.F->G == 0) {
         k_fill_u32<<<grid_for(c, Gp), ST, 0, c.stream>>>(link, Gp, NONE); c.launches++;
         return cudaGetLastError();
     }
@@ -246,8 +241,8 @@ cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
             uint32_t *dense = nullptr;
             GJ_CUDA_TRY(dalloc(c, &dense, range));
             GJ_CUDA_TRY(cudaMemsetAsync(dense, 0xFF, sizeof(uint32_t) * range, c.stream));
-            k_dense_fill<<<grid_for(c, ch.S), ST, 0, c.stream>>>(
-                ch.F->gkey + (int64_t)col * ch.F->G, ch.seg_first, ch.S, ch.R->kmin[col], dense); c.launches++;
+            k_dense_fill<<<grid_for(c, ch.F->G), ST, 0, c.stream>>>(
+                ch.F->gkey + (int64_t)col * ch.F->G, ch.seg_first, ch.S_dev, ch.R->kmin[col], dense); c.launches++;
             k_link_dense<<<grid_for(c, Gp), ST, 0, c.stream>>>(
                 t.F->gkey + (int64_t)ch.sep_cols_parent[0] * Gp, Gp, ch.R->kmin[col],
                 (uint64_t)range, dense, link); c.launches++;
@@ -258,7 +253,7 @@ cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
     }
     k_link_search<<<grid_for(c, Gp), ST, 0, c.stream>>>(key_cols(t, ch.sep_cols_parent), Gp,
                                                         key_cols(ch, ch.sep_cols), ch.seg_first,
-                                                        ch.S, link); c.launches++;
+                                                        ch.S_dev, link); c.launches++;
     return cudaGetLastError();
 }
 
@@ -266,6 +261,8 @@ cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
 
 void query_free_summary(Ctx &c, QueryState &q) {
     for (auto &t : q.r) {
+        dfree(c, t.S_dev);
+        dfree(c, t.L_dev);
         dfree(c, t.seg_id);
         dfree(c, t.seg_first);
         for (auto &l : t.link) dfree(c, l);
@@ -279,8 +276,6 @@ void query_free_summary(Ctx &c, QueryState &q) {
         dfree(c, t.loff);
         dfree(c, t.lw);
         dfree(c, t.lseg_first);
-        t.L = 0;
-        t.S = 0;
     }
     q.summarized = false;
 }
@@ -289,10 +284,13 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
     Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;
-#define TRY(x)                                  \
-    do {                                        \
-        e = (x);                                \
-        if (e != cudaSuccess) goto fail;        \
+#define TRY(x)                                                 \
+    do {                                                       \
+        e = (x);                                               \
+        if (e != cudaSuccess) {                                \
+            note_cuda_error(e, __FILE__, __LINE__);            \
+            goto fail;                                         \
+        }                                                      \
     } while (0)
     {
         // segments of every non-root relation, then links parent -> child
@@ -320,25 +318,16 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             k_weights<<<grid_for(c, G), ST, 0, c.stream>>>(t.F->gstart, G, cs, t.w); c.launches++;
             TRY(cudaGetLastError());
             if (t.parent >= 0) {
-                // heads of separator segments, re-derived from seg_id
                 uint8_t *heads = nullptr;
                 TRY(dalloc(c, &heads, G));
                 k_seg_heads<<<grid_for(c, G), ST, 0, c.stream>>>(key_cols(t, t.sep_cols), G, heads); c.launches++;
-                TRY(dalloc(c, &t.msg, t.S));
+                TRY(dalloc(c, &t.msg, G));      // S <= G segments
                 TRY(scan_u64_sat(c, t.w, heads, t.off, G, nullptr, t.msg, t.seg_id));
                 dfree(c, heads);
             } else {
                 TRY(scan_u64_sat(c, t.w, nullptr, t.off, G, total_dev, nullptr, nullptr));
             }
         }
-        {
-            uint64_t *h = c.pinned;
-            TRY(cudaMemcpyAsync(h, total_dev, 8, cudaMemcpyDeviceToHost, c.stream));
-            TRY(cudaStreamSynchronize(c.stream));
-            q.total = q.r[0].F->G ? h[0] : 0;
-            dfree(c, total_dev);
-        }
-        q.overflow = (q.total == SAT);
         // downward, root to leaves (preorder)
         for (int pi = 0; pi < q.k; pi++) {
             QRel &t = q.r[q.pre[pi]];
@@ -353,12 +342,13 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             std::vector<unsigned int *> carries(cs.n);
             for (int ci = 0; ci < cs.n; ci++) {
                 QRel &ch = q.r[t.children[ci]];
+                const int64_t Sc = std::max<int64_t>(ch.F->G, 1);
                 cs.link[ci] = t.link[ci];
                 cs.msg[ci] = ch.msg;
-                TRY(dalloc(c, &los[ci], ch.S));
-                TRY(dalloc(c, &carries[ci], ch.S));
-                TRY(cudaMemsetAsync(los[ci], 0, 8 * std::max<int64_t>(ch.S, 1), c.stream));
-                TRY(cudaMemsetAsync(carries[ci], 0, 4 * std::max<int64_t>(ch.S, 1), c.stream));
+                TRY(dalloc(c, &los[ci], Sc));
+                TRY(dalloc(c, &carries[ci], Sc));
+                TRY(cudaMemsetAsync(los[ci], 0, 8 * Sc, c.stream));
+                TRY(cudaMemsetAsync(carries[ci], 0, 4 * Sc, c.stream));
                 cs.lo[ci] = los[ci];
                 cs.carry[ci] = carries[ci];
             }
@@ -366,9 +356,9 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             TRY(cudaGetLastError());
             for (int ci = 0; ci < cs.n; ci++) {
                 QRel &ch = q.r[t.children[ci]];
-                TRY(dalloc(c, &ch.down, ch.S));
-                k_down_finalize<<<grid_for(c, ch.S), ST, 0, c.stream>>>(los[ci], carries[ci], ch.S,
-                                                                      ch.down); c.launches++;
+                TRY(dalloc(c, &ch.down, ch.F->G));
+                k_down_finalize<<<grid_for(c, ch.F->G), ST, 0, c.stream>>>(los[ci], carries[ci],
+                                                                         ch.S_dev, ch.down); c.launches++;
                 dfree(c, los[ci]);
                 dfree(c, carries[ci]);
             }
@@ -378,37 +368,42 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             QRel &t = q.r[i];
             const int64_t G = t.F->G;
             uint8_t *f = nullptr;
-            uint32_t *lidx = nullptr, *cnt = nullptr;
+            uint32_t *lidx = nullptr;
             TRY(dalloc(c, &f, G));
             TRY(dalloc(c, &lidx, G));
-            TRY(dalloc(c, &cnt, 1));
+            TRY(dalloc(c, &t.L_dev, 1));
             k_nonzero<<<grid_for(c, G), ST, 0, c.stream>>>(t.w, G, f); c.launches++;
-            TRY(scan_u32(c, nullptr, f, lidx, G, cnt));
-            uint32_t L = 0;
-            TRY(readback_u32(c, cnt, &L));
-            t.L = L;
-            TRY(dalloc(c, &t.lgid, t.L));
-            TRY(dalloc(c, &t.loff, t.L));
-            TRY(dalloc(c, &t.lw, t.L));
+            TRY(scan_u32(c, nullptr, f, lidx, G, t.L_dev));
+            TRY(dalloc(c, &t.lgid, G));        // L <= G live groups
+            TRY(dalloc(c, &t.loff, G));
+            TRY(dalloc(c, &t.lw, G));
             k_live_compact<<<grid_for(c, G), ST, 0, c.stream>>>(f, lidx, t.w, t.off, G, t.lgid,
                                                                 t.loff, t.lw); c.launches++;
             if (t.parent >= 0) {
-                TRY(dalloc(c, &t.lseg_first, t.S + 1));
-                k_live_segs<<<grid_for(c, t.S), ST, 0, c.stream>>>(t.seg_first, lidx, t.S, t.L,
-                                                                  t.lseg_first); c.launches++;
+                TRY(dalloc(c, &t.lseg_first, G + 1));
+                k_live_segs<<<grid_for(c, G), ST, 0, c.stream>>>(t.seg_first, lidx, t.S_dev,
+                                                                t.L_dev, t.lseg_first); c.launches++;
             }
             TRY(cudaGetLastError());
             dfree(c, f);
             dfree(c, lidx);
-            dfree(c, cnt);
         }
-        // device-side errors
+        // the one synchronisation: |Q| and the device error word
         {
-            uint32_t err = 0;
-            TRY(readback_u32(c, c.err, &err));
-            if (err & ERRF_TIMEOUT) return GJ_ERR_TIMEOUT;
-            if (err) return GJ_ERR_CUDA;
+            uint64_t *h = c.pinned;
+            h[0] = 0;
+            if (q.r[0].F->G) TRY(cudaMemcpyAsync(h, total_dev, 8, cudaMemcpyDeviceToHost, c.stream));
+            TRY(cudaMemcpyAsync(h + 1, c.err, 4, cudaMemcpyDeviceToHost, c.stream));
+            TRY(cudaStreamSynchronize(c.stream));
+            q.total = h[0];
+            uint32_t err = (uint32_t)(h[1] & 0xffffffffu);
+            dfree(c, total_dev);
+            if (err) {
+                cudaMemsetAsync(c.err, 0, 4, c.stream);
+                return (err & ERRF_TIMEOUT) ? GJ_ERR_TIMEOUT : GJ_ERR_CUDA;
+            }
         }
+        q.overflow = (q.total == SAT);
     }
 #undef TRY
     q.summarized = true;
