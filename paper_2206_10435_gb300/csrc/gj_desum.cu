@@ -189,7 +189,7 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             const uint32_t g = s.lgid[h];
             const uint64_t unit = unit_in[i];
             o.A[slot] = s.A[i] + unit * s.loff[h];
-            o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
+            if (o.W) o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
             for (int p = 0; p < j; p++) o.grp[p][slot] = s.grp[p][i];
             o.grp[j][slot] = g;
             if (o.lh) o.lh[slot] = h;
@@ -261,11 +261,12 @@ int child_index(const QRel &parent, int child_pos) {
     return -1;
 }
 
-cudaError_t frontier_alloc(Ctx &c, Frontier &f, int64_t cap, int depth, bool keep_last) {
+cudaError_t frontier_alloc(Ctx &c, Frontier &f, int64_t cap, int depth, bool keep_last,
+                           bool need_w = true) {
     f.cap = cap;
     GJ_CUDA_TRY(dalloc(c, &f.F_dev, 1));
     GJ_CUDA_TRY(dalloc(c, &f.A, cap));
-    GJ_CUDA_TRY(dalloc(c, &f.W, cap));
+    if (need_w) GJ_CUDA_TRY(dalloc(c, &f.W, cap));
     f.grp.assign(depth, nullptr);
     for (int p = 0; p < depth; p++) GJ_CUDA_TRY(dalloc(c, &f.grp[p], cap));
     if (keep_last) {
@@ -333,7 +334,8 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         GJ_CUDA_TRY(dalloc(c, &slot_first, ceil_div(cap, EXP_TILE) + 1));
         const bool last = (j == depth - 1);
         Frontier nxt;
-        GJ_CUDA_TRY(frontier_alloc(c, nxt, cap, j + 1, last && keep_last));
+        // the last frontier's W (counts of the chosen groups) is not used
+        GJ_CUDA_TRY(frontier_alloc(c, nxt, cap, j + 1, last && keep_last, !last));
         k_expand_count<<<grid_for(c, cap), DT, 0, c.stream>>>(s, cur.F_dev, row0, row_end, cnt, lo,
                                                             unit, c.err); c.launches++;
         GJ_CUDA_TRY(cudaGetLastError());

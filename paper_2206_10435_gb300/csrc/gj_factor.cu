@@ -110,6 +110,38 @@ __global__ void k_group_compact(ColSet cs, const uint32_t *__restrict__ perm,
     if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
 }
 
+// sorted[c*n + i] = col_c[perm[i]]: the key columns in sorted order, one
+// random read per column and row (used when the key spans several words)
+__global__ void k_gather_cols(ColSet cs, const uint32_t *__restrict__ perm, int64_t n,
+                              int32_t *__restrict__ sorted) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        uint32_t r = perm[i];
+        for (int c = 0; c < cs.ncol; c++) sorted[(int64_t)c * n + i] = cs.col[c][r];
+    }
+}
+
+__global__ void k_heads_sorted(const int32_t *__restrict__ sorted, int nk, int64_t n, uint8_t *head) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        uint8_t h = (i == 0);
+        for (int c = 0; c < nk && !h; c++)
+            h = sorted[(int64_t)c * n + i] != sorted[(int64_t)c * n + i - 1];
+        head[i] = h;
+    }
+}
+
+__global__ void k_group_compact_sorted(const int32_t *__restrict__ sorted, int nk,
+                                       const uint8_t *__restrict__ head,
+                                       const uint32_t *__restrict__ gid, int64_t n, int64_t G,
+                                       uint32_t *gstart, int32_t *gkey) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        if (!head[i]) continue;
+        uint32_t g = gid[i];
+        gstart[g] = (uint32_t)i;
+        for (int c = 0; c < nk; c++) gkey[(int64_t)c * G + g] = sorted[(int64_t)c * n + i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
+}
+
 template <class T>
 __global__ void k_gather(const T *__restrict__ src, const uint32_t *__restrict__ perm, int64_t n,
                          T *__restrict__ dst) {
@@ -227,10 +259,15 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
     ColSet all{};
     all.ncol = R.nk;
     for (int i = 0; i < R.nk; i++) all.col[i] = R.key[i];
+    int32_t *sorted = nullptr;
     if (words.size() == 1) {
         k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(keys, n, head); c.launches++;
     } else {
-        k_heads_gather<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, head); c.launches++;
+        // the key spans several words: bring the columns into sorted order
+        // once, then find heads and groups with sequential reads
+        GJ_CUDA_TRY(dalloc(c, &sorted, (size_t)R.nk * n));
+        k_gather_cols<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, sorted); c.launches++;
+        k_heads_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, R.nk, n, head); c.launches++;
     }
     GJ_CUDA_TRY(cudaGetLastError());
     GJ_CUDA_TRY(scan_u32(c, nullptr, head, gid, n, gcount));
@@ -240,8 +277,14 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
     F.G = hg[0];
     GJ_CUDA_TRY(dalloc(c, &F.gstart, F.G + 1));
     GJ_CUDA_TRY(dalloc(c, &F.gkey, (size_t)R.nk * F.G));
-    k_group_compact<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, head, gid, n, F.G, F.gstart,
-                                                         F.gkey); c.launches++;
+    if (sorted) {
+        k_group_compact_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, R.nk, head, gid, n, F.G,
+                                                                    F.gstart, F.gkey); c.launches++;
+        dfree(c, sorted);
+    } else {
+        k_group_compact<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, head, gid, n, F.G, F.gstart,
+                                                             F.gkey); c.launches++;
+    }
     GJ_CUDA_TRY(cudaGetLastError());
     for (int p = 0; p < R.np; p++) {
         void *d = nullptr;

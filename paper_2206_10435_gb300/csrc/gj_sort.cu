@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(RS_RADIX) k_hist_to_base(uint32_t *hist) {
 }
 
 template <bool VALS>
-__global__ void __launch_bounds__(RS_THREADS)
+__global__ void __launch_bounds__(RS_THREADS, 3)
 k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
              const uint32_t *__restrict__ bucket_base, uint32_t *tile_counter,
