@@ -39,11 +39,12 @@ def parse():
     p.add_argument("--impl", default="gj", choices=["gj", "reference"])
     p.add_argument("--workload", default="chain5_zipf",
                    choices=["chain5_zipf", "chain3_uniform", "star_poisson", "batch", "serve"])
-    p.add_argument("--rates", default="100,200,500,1000,2000,5000",
+    p.add_argument("--rates", default="100,200,500,1000,2000,5000,10000",
                    help="serve workload: offered arrival rates (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--slots", type=int, default=16)
     p.add_argument("--pool", type=int, default=512, help="serve workload: distinct small queries")
+    p.add_argument("--serve-engine", default="native", choices=["native", "python"])
     p.add_argument("--queries", type=int, default=4096, help="batch workload: queries")
     p.add_argument("--rows", type=int, default=10**7)
     p.add_argument("--domain", type=int, default=10**6)
@@ -495,16 +496,26 @@ def run_serve(a, rank, world, local):
     sweep = []
     clocks = ClockSampler(local)
     clocks.start()
+    from paper_2206_10435_gb300.serve import native_latency_stats
     for rate in rates:
-        n = int(min(max(rate * a.serve_seconds, 100), 10000))
+        n = int(min(max(rate * a.serve_seconds, 100), 20000))
         picks = [large_ids[int(rng.integers(0, len(large_ids)))] if rng.random() < 0.01
                  else small_ids[int(rng.integers(0, len(small_ids)))] for _ in range(n)]
-        eng = GJEngine(ctx, a.slots, chunk_rows=1 << 20)
-        srv = Server(eng, n_slots=a.slots, hbm_budget=150 * 10**9)
-        reqs = run_stream(srv, picks, poisson_arrivals(rate, n, seed=int(rate)))
-        st = latency_stats(reqs)
-        st.update({"offered_qps": rate, "requests": n, "peak_in_flight": srv.peak_in_flight,
-                   "peak_admitted_gb": srv.peak_used / 1e9})
+        offsets = poisson_arrivals(rate, n, seed=int(rate))
+        if a.serve_engine == "native":
+            srv = gj.NativeServer(ctx, n_slots=a.slots, hbm_budget=150 * 10**9, chunk_rows=1 << 20)
+            res, sst = srv.run(picks, offsets)
+            srv.close()
+            st = native_latency_stats(res)
+            st.update({"offered_qps": rate, "requests": n, "peak_in_flight": sst["peak_in_flight"],
+                       "peak_admitted_gb": sst["peak_admitted_bytes"] / 1e9})
+        else:
+            eng = GJEngine(ctx, a.slots, chunk_rows=1 << 20)
+            srv = Server(eng, n_slots=a.slots, hbm_budget=150 * 10**9)
+            reqs = run_stream(srv, picks, offsets)
+            st = latency_stats(reqs)
+            st.update({"offered_qps": rate, "requests": n, "peak_in_flight": srv.peak_in_flight,
+                       "peak_admitted_gb": srv.peak_used / 1e9})
         sweep.append(st)
     clk = clocks.stop()
     best = max((s.get("qps") or 0) for s in sweep)
@@ -516,7 +527,7 @@ def run_serve(a, rank, world, local):
                                    f"each; {a.pool} queries of the batch distribution + 1% "
                                    "4-table chains of 1e7 rows (Zipf 1.1 over 1e6); summary + "
                                    "first 2^20-row chunk per request; 150 GB HBM budget"),
-                      "slots": a.slots, "factor_build_s": warm_s},
+                      "slots": a.slots, "engine": a.serve_engine, "factor_build_s": warm_s},
            "sweep": sweep, "clocks": clk}
     if rank == 0:
         print(json.dumps(out), flush=True)

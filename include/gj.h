@@ -263,6 +263,43 @@ gj_status gj_batch_run(gj_batch *batch, int32_t use_graph, uint64_t *totals_dev,
 void gj_batch_destroy(gj_batch *batch);
 
 /*
+ * Native serving runtime (Section 4.1's pre-built potentials kept resident,
+ * queries answered as they arrive).  gj_server_run replays a trace of
+ * n_requests queries -- request i is the relations rel_ids[query_off[i] ..
+ * query_off[i+1]), arriving arrival_offsets[i] seconds after the start --
+ * and returns when all are answered.  A dispatcher thread releases and
+ * plans requests at their arrival times; admission is FIFO while the
+ * estimated device memory of the admitted requests stays under hbm_budget;
+ * n_slots slot threads, each with its own stream, summarise a request and
+ * desummarise its first chunk_rows result rows, so concurrent requests
+ * overlap on the device.  results[i] receives |Q|, the status, the first
+ * chunk's row count and an order-independent 64-bit hash of its columns,
+ * and arrival / admission / summary / first-chunk times (steady clock, s).
+ * Relations must be loaded, and their factors should be built, beforehand.
+ */
+typedef struct gj_server gj_server;
+typedef struct {
+    uint64_t total;
+    int32_t status;
+    int32_t slot;
+    uint64_t chunk_rows;
+    uint64_t chunk_hash;
+    uint64_t est_bytes;
+    double t_arrival, t_admit, t_summary, t_chunk;
+} gj_request_result;
+typedef struct {
+    int32_t peak_in_flight;
+    uint64_t peak_admitted_bytes;
+    double wall_s;
+} gj_server_stats;
+gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, uint64_t chunk_rows,
+                           gj_server **out);
+gj_status gj_server_run(gj_server *server, int32_t n_requests, const int32_t *rel_ids,
+                        const int32_t *query_off, const double *arrival_offsets,
+                        gj_request_result *results, gj_server_stats *stats);
+void gj_server_destroy(gj_server *server);
+
+/*
  * Factor construction without any device allocation.  The paper has no
  * counterpart; this exists for callers that cannot allocate device memory:
  * a database engine or serving process that hands all device memory to its

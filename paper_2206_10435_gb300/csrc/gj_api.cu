@@ -421,6 +421,7 @@ gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
     if (!q) return GJ_ERR_INVALID;
     QueryState &s = q->s;
     DeviceGuard g(s.cs->c.device);
+    if (s.exec && !s.own) return GJ_ERR_STATE;   // runs on a context lent by a server
     if (!s.own) {
         std::unique_ptr<Ctx> o(new Ctx());
         const Ctx &base = s.cs->c;
@@ -437,6 +438,7 @@ gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
         // the query's earlier work (if any) ran on the context's stream
         cudaStreamSynchronize(base.stream);
         s.own = std::move(o);
+        s.exec = s.own.get();
     } else {
         cudaStreamSynchronize(s.own->stream);
     }

@@ -100,7 +100,8 @@ struct QueryState {
     // optional execution context of this query alone (own stream, readback
     // buffer and error word; shares the context's pool and factors)
     std::unique_ptr<Ctx> own;
-    Ctx &ctx() { return own ? *own : cs->c; }
+    Ctx *exec = nullptr;               // own.get(), or a context lent by the server
+    Ctx &ctx() { return exec ? *exec : cs->c; }
     int k = 0;
     std::vector<QRel> r;
     std::vector<int> pre;              // preorder of positions

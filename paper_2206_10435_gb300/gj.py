@@ -50,6 +50,19 @@ class Profile(ctypes.Structure):
                 ("emit_bytes", ctypes.c_uint64), ("expand_ms", ctypes.c_double)]
 
 
+class RequestResult(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_uint64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("chunk_rows", ctypes.c_uint64), ("chunk_hash", ctypes.c_uint64),
+                ("est_bytes", ctypes.c_uint64), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_summary", ctypes.c_double),
+                ("t_chunk", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("peak_in_flight", ctypes.c_int32), ("peak_admitted_bytes", ctypes.c_uint64),
+                ("wall_s", ctypes.c_double)]
+
+
 class QuerySizes(ctypes.Structure):
     _fields_ = [("n_rel", ctypes.c_int32), ("n_vars", ctypes.c_int32),
                 ("var_attr", ctypes.c_int32 * 64), ("n_cols", ctypes.c_int32),
@@ -110,6 +123,14 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_int32)]),
         "gj_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
         "gj_batch_destroy": (None, [_P]),
+        "gj_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.POINTER(_P)]),
+        "gj_server_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(RequestResult),
+                                         ctypes.POINTER(ServerStats)]),
+        "gj_server_destroy": (None, [_P]),
         "gj_desummarize": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(_P), ctypes.POINTER(_P),
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -362,6 +383,45 @@ class Batch:
     def close(self):
         if self.h:
             lib().gj_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NativeServer:
+    """The native serving runtime (gj_server_*): replays arrival traces."""
+
+    def __init__(self, ctx: Context, n_slots: int = 16, hbm_budget: int = 150 * 10**9,
+                 chunk_rows: int = 1 << 20):
+        self.ctx = ctx
+        h = _P()
+        _check(lib().gj_server_create(ctx.h, n_slots, hbm_budget, chunk_rows, ctypes.byref(h)),
+               "gj_server_create")
+        self.h = h
+
+    def run(self, queries_rel_ids, arrival_offsets):
+        """queries_rel_ids[i] arrives arrival_offsets[i] s after the start.
+        Returns (list of result dicts, stats dict)."""
+        n = len(queries_rel_ids)
+        flat = [r for q in queries_rel_ids for r in q]
+        off = [0]
+        for q in queries_rel_ids:
+            off.append(off[-1] + len(q))
+        arr = (ctypes.c_double * max(n, 1))(*[float(x) for x in arrival_offsets])
+        res = (RequestResult * max(n, 1))()
+        st = ServerStats()
+        _check(lib().gj_server_run(self.h, n, _i32(flat), _i32(off), arr, res, ctypes.byref(st)),
+               "gj_server_run")
+        out = [{f: getattr(res[i], f) for f, _ in RequestResult._fields_} for i in range(n)]
+        return out, {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().gj_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -167,6 +167,21 @@ def run_stream(server: Server, queries, offsets):
     return reqs
 
 
+def native_latency_stats(results):
+    """latency_stats for the result dicts of gj.NativeServer.run."""
+    import numpy as np
+    ok = [r for r in results if r["status"] in (0, 4)]   # GJ_OK, GJ_ERR_OVERFLOW
+    if not ok:
+        return {"completed": 0}
+    s = np.array([r["t_summary"] - r["t_arrival"] for r in ok]) * 1000
+    c = np.array([r["t_chunk"] - r["t_arrival"] for r in ok]) * 1000
+    span = max(r["t_chunk"] for r in ok) - min(r["t_arrival"] for r in ok)
+    return {"completed": len(ok), "failed": len(results) - len(ok),
+            "qps": len(ok) / span if span > 0 else None,
+            "p50_summary_ms": float(np.percentile(s, 50)), "p99_summary_ms": float(np.percentile(s, 99)),
+            "p50_first_chunk_ms": float(np.percentile(c, 50)), "p99_first_chunk_ms": float(np.percentile(c, 99))}
+
+
 def latency_stats(reqs):
     import numpy as np
     ok = [r for r in reqs if r.status in ("ok", "overflow")]
