@@ -184,11 +184,13 @@ def batch_queries(seed: int = SEED_BASE + 3, n_queries: int = 4096,
 
 
 def random_tree_query(seed: int, n_rel: int, max_rows: int = 6, domain: int = 3,
-                      max_new: int = 2, payload: bool = True, min_rows: int = 0) -> Query:
+                      max_new: int = 2, payload: bool = True, min_rows: int = 0,
+                      max_shared: int = 1, spread: int = 0) -> Query:
     """Small random acyclic query: relation j > 0 attaches to a random earlier
-    relation, shares one attribute of it, and adds 0..max_new attributes of
-    its own.  Values are uniform over a small domain so that joins match,
-    repeat and die."""
+    relation, shares 1..max_shared of its attributes, and adds 0..max_new
+    attributes of its own.  Values are uniform over a small domain so that
+    joins match, repeat and die; spread > 0 maps value v to v * spread - 2^30
+    (same join structure, values far apart in the int32 range)."""
     rng = np.random.default_rng(seed)
     next_attr = 0
     rel_attrs = []
@@ -199,17 +201,20 @@ def random_tree_query(seed: int, n_rel: int, max_rows: int = 6, domain: int = 3,
             next_attr += na
         else:
             par = int(rng.integers(0, j))
-            shared = int(rng.choice(rel_attrs[par]))
+            ns = int(rng.integers(1, min(max_shared, len(rel_attrs[par])) + 1))
+            shared = [int(x) for x in rng.choice(rel_attrs[par], size=ns, replace=False)]
             na = int(rng.integers(0, max_new + 1))
             new = list(range(next_attr, next_attr + na))
             next_attr += na
-            attrs = [shared] + new
+            attrs = shared + new
             rng.shuffle(attrs)
         rel_attrs.append([int(a) for a in attrs])
     rels = []
     for j, attrs in enumerate(rel_attrs):
         n = int(rng.integers(min_rows, max_rows + 1))
         cols = [rng.integers(-1, domain - 1, size=n, dtype=np.int32) for _ in attrs]
+        if spread:
+            cols = [(c.astype(np.int64) * spread - 2**30).astype(np.int32) for c in cols]
         pays = []
         if payload:
             pays = [_payload(rng, n, np.int32), _payload(rng, n, np.int64)]

@@ -278,3 +278,36 @@ def test_star_full_size(ctx):
         done += out[0].shape[0]
     assert done == total
     run.close()
+
+
+def shape_queries():
+    qs = []
+    for seed in range(40):
+        n_rel = 2 + seed % 4
+        qs.append(G.random_tree_query(500 + seed, n_rel, max_rows=5 if n_rel <= 3 else 4,
+                                      domain=3, max_new=2, min_rows=1, max_shared=3,
+                                      spread=(seed % 3) * 600_000_007 % 2_000_000_000 // 3))
+    return qs
+
+
+@pytest.mark.parametrize("q", shape_queries(), ids=lambda q: q.name)
+def test_multi_attribute_separators_and_wide_ranges(ctx, q):
+    # separators of 2-3 attributes (binary-search links) and keys spread over
+    # the int32 range (no dense link table)
+    full_parity(ctx, q, windows=[(0, 1), (2, 3)])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 3, 4, 5, 6])
+def test_many_relations(ctx, seed):
+    # 9-12 relations: beyond the templated emit kernels (generic path)
+    q = G.random_tree_query(900 + seed, 9 + seed % 4, max_rows=5, domain=2, max_new=1,
+                            min_rows=4)
+    assert O.count(q).total > 0
+    full_parity(ctx, q, windows=[(0, 7), (5, 1000)])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_larger_random_trees_with_multi_attribute_separators(ctx, seed):
+    q = G.random_tree_query(1300 + seed, 3 + seed % 3, max_rows=80, domain=5, max_new=2,
+                            min_rows=30, max_shared=2, spread=seed * 1_000_003)
+    full_parity(ctx, q, windows=[(0, 1000), (1001, 1025)])

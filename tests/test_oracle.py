@@ -288,3 +288,25 @@ def test_aligned_zipf_chain_overflows():
     q2 = G.chain5_zipf(rows=10**5, domain=10**5)
     c2 = O.count(q2)
     assert not c2.overflow and 0 < c2.total < CAP
+
+
+# ------------------------------------------------------------------ wider shapes
+
+def _shape_queries():
+    qs = []
+    for seed in range(40):
+        n_rel = 2 + seed % 4
+        qs.append(G.random_tree_query(500 + seed, n_rel, max_rows=5 if n_rel <= 3 else 4,
+                                      domain=3, max_new=2, min_rows=1, max_shared=3,
+                                      spread=(seed % 3) * 600_000_007 % 2_000_000_000 // 3))
+    return qs
+
+
+@pytest.mark.parametrize("q", _shape_queries(), ids=lambda q: q.name)
+def test_oracle_matches_nested_loops_multi_attribute_separators(q):
+    pl = O.plan(q)
+    bf = canonical(q, brute_force(q), pl.V)
+    c = O.count(q)
+    assert c.total == len(bf)
+    if bf:
+        assert [tuple(t) for t in O.join(q).rowids.tolist()] == [tuple(t) for t in bf]
