@@ -263,6 +263,22 @@ gj_status gj_batch_run(gj_batch *batch, int32_t use_graph, uint64_t *totals_dev,
 void gj_batch_destroy(gj_batch *batch);
 
 /*
+ * Compute-and-reuse (Sections 3.6 and 4, Tables 3-4): instead of storing the
+ * join result, store its summary and desummarise it later.
+ * gj_summary_save writes everything desummarisation needs -- per relation
+ * the factor (row order, group starts and keys, payloads in group order)
+ * and the summary arrays, plus the join tree and output layout -- to the
+ * file `path` and reports its size in *bytes.  Requires gj_summarize.
+ * gj_summary_load reads such a file into a new query on `ctx` that owns its
+ * device copies and needs none of the original relations: gj_desummarize,
+ * gj_level, gj_summary_groups and gj_query_sizes work on it as on the
+ * original, and gj_summarize returns the stored |Q|.  A file that is not a
+ * complete summary gives GJ_ERR_INVALID.
+ */
+gj_status gj_summary_save(gj_query *q, const char *path, uint64_t *bytes);
+gj_status gj_summary_load(gj_ctx *ctx, const char *path, gj_query **out);
+
+/*
  * Native serving runtime (Section 4.1's pre-built potentials kept resident,
  * queries answered as they arrive).  gj_server_run replays a trace of
  * n_requests queries -- request i is the relations rel_ids[query_off[i] ..

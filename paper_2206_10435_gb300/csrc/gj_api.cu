@@ -408,6 +408,9 @@ void gj_query_destroy(gj_query *q) {
     if (!q) return;
     DeviceGuard g(q->s.cs->c.device);
     query_free_summary(q->s.ctx(), q->s);
+    for (auto &R : q->s.loaded)
+        for (auto &kv : R->factors) factor_free(q->s.ctx(), *kv.second);
+    q->s.loaded.clear();
     if (q->s.own) {
         Ctx &o = *q->s.own;
         cudaStreamSynchronize(o.stream);
@@ -468,6 +471,10 @@ gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out) {
 
 gj_status gj_summarize(gj_query *q, uint64_t *total) {
     if (!q || !total) return GJ_ERR_INVALID;
+    if (!q->s.loaded.empty()) {   // a loaded summary is already complete
+        *total = q->s.total;
+        return q->s.overflow ? GJ_ERR_OVERFLOW : GJ_OK;
+    }
     DeviceGuard g(q->s.cs->c.device);
     cudaMemsetAsync(q->s.ctx().err, 0, 4, q->s.ctx().stream);
     return summarize(q->s, total);

@@ -111,6 +111,8 @@ struct QueryState {
     bool summarized = false;
     bool overflow = false;
     uint64_t total = 0;
+    // relations (with their factors) owned by a summary loaded from a file
+    std::vector<std::unique_ptr<Relation>> loaded;
 };
 
 }  // namespace gj

@@ -131,6 +131,8 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(RequestResult),
                                          ctypes.POINTER(ServerStats)]),
         "gj_server_destroy": (None, [_P]),
+        "gj_summary_save": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_uint64)]),
+        "gj_summary_load": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.POINTER(_P)]),
         "gj_desummarize": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.POINTER(_P), ctypes.POINTER(_P),
                                           ctypes.POINTER(ctypes.c_uint64)]),
@@ -249,12 +251,15 @@ class Context:
 
 
 class Query:
-    def __init__(self, ctx: Context, rel_ids):
+    def __init__(self, ctx: Context, rel_ids=None, handle=None):
         self.ctx = ctx
-        ids = _i32(list(rel_ids))
-        h = _P()
-        _check(lib().gj_query_create(ctx.h, ids, len(rel_ids), ctypes.byref(h)),
-               "gj_query_create")
+        if handle is not None:
+            h = handle
+        else:
+            ids = _i32(list(rel_ids))
+            h = _P()
+            _check(lib().gj_query_create(ctx.h, ids, len(rel_ids), ctypes.byref(h)),
+                   "gj_query_create")
         self.h = h
         s = QuerySizes()
         _check(lib().gj_query_sizes(self.h, ctypes.byref(s)), "gj_query_sizes")
@@ -276,6 +281,24 @@ class Query:
             self.close()
         except Exception:
             pass
+
+    def save(self, path: str) -> int:
+        """Stores the summary (gj_summary_save); returns the file size."""
+        n = ctypes.c_uint64()
+        _check(lib().gj_summary_save(self.h, path.encode(), ctypes.byref(n)), "gj_summary_save")
+        return int(n.value)
+
+    @staticmethod
+    def load(ctx: "Context", path: str) -> "Query":
+        """A query from a stored summary (gj_summary_load)."""
+        h = _P()
+        _check(lib().gj_summary_load(ctx.h, path.encode(), ctypes.byref(h)), "gj_summary_load")
+        q = Query(ctx, handle=h)
+        t = ctypes.c_uint64()
+        st = lib().gj_summarize(h, ctypes.byref(t))
+        q.total = int(t.value)
+        q.status = st
+        return q
 
     def set_stream(self, stream):
         """Run this query's later work on its own torch stream."""
