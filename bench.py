@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--impl", default="gj", choices=["gj", "reference"])
     p.add_argument("--workload", default="chain5_zipf",
                    choices=["chain5_zipf", "chain3_uniform", "star_poisson", "batch", "serve",
-                            "reuse"])
+                            "reuse", "sensitivity"])
     p.add_argument("--rates", default="100,200,500,1000,2000,5000,10000",
                    help="serve workload: offered arrival rates (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -239,7 +239,7 @@ def reduce_over_ranks(dist, elapsed_ms: float, rows: int, device):
 
 
 DEFAULT_SAMPLE = {"chain5_zipf": 20000, "chain3_uniform": 10**4, "star_poisson": 10**6,
-                  "batch": 0, "serve": 0, "reuse": 0}
+                  "batch": 0, "serve": 0, "reuse": 0, "sensitivity": 0}
 
 
 def main():
@@ -257,6 +257,8 @@ def main():
         return run_serve(a, rank, world, local)
     if a.workload == "reuse":
         return run_reuse(a, rank, world, local)
+    if a.workload == "sensitivity":
+        return run_sensitivity(a, rank, world, local)
 
     import numpy as np
     import torch
@@ -587,6 +589,73 @@ def run_reuse(a, rank, world, local):
            "result_to_summary_ratio": total * row_bytes / nbytes,
            "save_s": save_s, "load_s": load_s, "desummarise_s": desum_s,
            "note": "the file was just written, so the load reads from the page cache"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def time_query(ctx, q, stream, chunk, steps, warmup):
+    """Device time of the whole path on one query (factors, summary, every
+    result row), averaged over `steps` after `warmup` runs."""
+    import torch
+    from paper_2206_10435_gb300 import gj
+    dev = torch.device("cuda", ctx.device)
+    rels = [([torch.from_numpy(k).to(dev) for k in R.keys],
+             [torch.from_numpy(p).to(dev) for p in R.payloads], R.attrs) for R in q.relations]
+    bufs = None
+    out = {}
+    with torch.cuda.stream(stream):
+        for it in range(warmup + steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            ids = [ctx.load_relation(ks, attrs, ps) for ks, ps, attrs in rels]
+            qq = ctx.query(ids)
+            total = qq.summarize()
+            ev[1].record(stream)
+            if bufs is None:
+                bufs = qq.alloc_columns(min(chunk, total))
+            for r0 in range(0, total, chunk):
+                qq.desummarize(r0, chunk, out=bufs)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            groups = sum(qq.n_groups)
+            qq.close()
+            for i in ids:
+                ctx.release_relation(i)
+            if it >= warmup:
+                out.setdefault("summary_ms", 0.0)
+                out.setdefault("total_ms", 0.0)
+                out["summary_ms"] += ev[0].elapsed_time(ev[1]) / steps
+                out["total_ms"] += ev[0].elapsed_time(ev[2]) / steps
+    out.update({"join_size": total, "groups": groups, "rows": q.n_rows_total,
+                "tuples_per_s": total / (out["total_ms"] / 1000.0)})
+    return out
+
+
+def run_sensitivity(a, rank, world, local):
+    """Section 4.2: the same chain with every tuple duplicated (result
+    redundancy x 2^k) and with one more hop (more unneeded intermediate
+    results).  GJ's summary cost follows the input, its desummarisation the
+    result size, so neither form should change the rate of result rows."""
+    import torch
+    from paper_2206_10435_gb300 import datagen as G, gj
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(torch.device("cuda", local))
+    ctx = gj.Context(local, stream)
+    base = G.chain_sensitivity(rows=a.rows, domain=a.domain, s=a.zipf, hops=3)
+    variants = {"base_3hop": base, "dup_3hop": G.duplicate_rows(base),
+                "extra_hop_4hop": G.chain_sensitivity(rows=a.rows, domain=a.domain, s=a.zipf, hops=4)}
+    res = {name: time_query(ctx, q, stream, 1 << a.chunk_log2, a.steps, a.warmup)
+           for name, q in variants.items()}
+    out = {"metric": "result tuples materialised/s per variant (sensitivity, Section 4.2)",
+           "value": res["base_3hop"]["tuples_per_s"], "unit": "tuples/s", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": res["base_3hop"]["total_ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic",
+           "config": {"workload": (f"sensitivity: chain R_i(K_i-1,K_i), {a.rows} rows/table, Zipf("
+                                   f"{a.zipf}) over [0,{a.domain}), int64 payloads; base 3 tables, "
+                                   "every tuple duplicated, one extra hop")},
+           "variants": res}
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()

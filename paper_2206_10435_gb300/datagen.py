@@ -286,3 +286,24 @@ def chain_zipf_torch(seed: int, tables: int = 4, rows: int = 10**7, domain: int 
         return torch.randperm(domain, generator=g, device=device)[r].to(torch.int32)
 
     return [([i, i + 1], [keys(), keys()]) for i in range(tables)]
+
+
+def duplicate_rows(query: Query, times: int = 2) -> Query:
+    """Every relation with each row repeated `times` times (the "_dup" form of
+    the sensitivity study, Section 4.2): the join size grows by times^k while
+    the distinct key tuples stay the same."""
+    rels = []
+    for R in query.relations:
+        rels.append(Relation(R.name + "_dup", list(R.attrs),
+                             [np.tile(k, times) for k in R.keys],
+                             [np.tile(p, times) for p in R.payloads]))
+    return Query(query.name + "_dup", rels, dict(query.attr_names))
+
+
+def chain_sensitivity(seed: int = SEED_BASE + 7, rows: int = 10**6, domain: int = 10**5,
+                      s: float = 1.1, hops: int = 3) -> Query:
+    """The base chain of the sensitivity study: `hops` tables R_i(K_{i-1}, K_i)
+    with Zipf(s) keys (the shape of a user-item-friend chain); hops + 1 adds
+    one join and with it more unneeded intermediate results (Section 4.2)."""
+    return chain_query(f"sens{hops}", [rows] * hops, [domain] * (hops + 1), [s] * (hops + 1),
+                       np.int64, seed)

@@ -311,3 +311,14 @@ def test_larger_random_trees_with_multi_attribute_separators(ctx, seed):
     q = G.random_tree_query(1300 + seed, 3 + seed % 3, max_rows=80, domain=5, max_new=2,
                             min_rows=30, max_shared=2, spread=seed * 1_000_003)
     full_parity(ctx, q, windows=[(0, 1000), (1001, 1025)])
+
+
+@pytest.mark.parametrize("hops", [3, 4])
+def test_sensitivity_variants(ctx, hops):
+    # Section 4.2: the duplicated form multiplies |Q| by 2^k; the extra hop
+    # adds a join; both stay exact
+    base = G.chain_sensitivity(rows=4000, domain=3000, hops=hops)
+    dup = G.duplicate_rows(base)
+    tb = full_parity(ctx, base, check_levels=False)
+    td = full_parity(ctx, dup, check_levels=False)
+    assert td == tb * 2 ** hops

@@ -310,3 +310,9 @@ def test_oracle_matches_nested_loops_multi_attribute_separators(q):
     assert c.total == len(bf)
     if bf:
         assert [tuple(t) for t in O.join(q).rowids.tolist()] == [tuple(t) for t in bf]
+
+
+def test_duplicated_tables_multiply_the_join_size():
+    base = G.chain_sensitivity(rows=2000, domain=500, hops=3)
+    assert O.count(G.duplicate_rows(base)).total == 8 * O.count(base).total
+    assert O.count(G.duplicate_rows(base, 3)).total == 27 * O.count(base).total
