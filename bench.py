@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--domain", type=int, default=10**6)
     p.add_argument("--zipf", type=float, default=1.1)
     p.add_argument("--chunk-log2", type=int, default=28)
+    p.add_argument("--emit-rpt", type=int, default=4, choices=[2, 4, 8],
+                   help="result rows per thread of the emit kernel")
     p.add_argument("--e2e-chunk-log2", type=int, default=24)
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
@@ -278,6 +280,7 @@ def main():
     in_bytes = sum(sum(t.numel() * t.element_size() for t in ks + ps) for ks, ps, _ in rels)
     stream = torch.cuda.Stream(dev)
     ctx = gj.Context(local, stream)
+    ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, a.emit_rpt)
     CH = 1 << a.chunk_log2
     out_bufs = None
     phase = {"build_ms": 0.0, "summary_ms": 0.0, "desum_ms": 0.0}

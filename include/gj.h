@@ -116,6 +116,16 @@ void gj_destroy(gj_ctx *ctx);
 gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
 
 /*
+ * Tuning options of a context (no counterpart in the paper).
+ * GJ_OPT_EMIT_ROWS_PER_THREAD: result rows each thread of the desummarise
+ * emit kernel writes, 2, 4 or 8 (default 4): fewer rows per thread means fewer
+ * registers and more threads in flight, more rows means fewer block
+ * lookups per row.  Takes effect for queries created afterwards.
+ */
+#define GJ_OPT_EMIT_ROWS_PER_THREAD 1
+gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value);
+
+/*
  * Profiling (no counterpart in the paper, which reports wall-clock times
  * only).  With out != NULL: synchronises the stream, writes the counters
  * accumulated since the previous read and resets them.  Then turns device

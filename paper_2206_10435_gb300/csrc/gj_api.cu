@@ -186,6 +186,16 @@ gj_status gj_profile(gj_ctx *ctx, int32_t enable, gj_profile_t *out) {
     return GJ_OK;
 }
 
+gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value) {
+    if (!ctx) return GJ_ERR_INVALID;
+    if (option == GJ_OPT_EMIT_ROWS_PER_THREAD) {
+        if (value != 2 && value != 4 && value != 8) return GJ_ERR_INVALID;
+        ctx->s.c.emit_rpt = (int)value;
+        return GJ_OK;
+    }
+    return GJ_ERR_INVALID;
+}
+
 gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream) {
     if (!ctx) return GJ_ERR_INVALID;
     DeviceGuard g(ctx->s.c.device);
@@ -431,6 +441,7 @@ gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
         o->device = base.device;
         o->pool = base.pool;
         o->num_sms = base.num_sms;
+        o->emit_rpt = base.emit_rpt;
         if (cudaMalloc((void **)&o->err, 16) != cudaSuccess ||
             cudaMallocHost((void **)&o->pinned, 1 << 16) != cudaSuccess) {
             cudaGetLastError();

@@ -1,6 +1,6 @@
 // gj_emit.cu -- desummarisation, the emit step (Section 3.6).
 //
-// Emission with 4 consecutive rows per thread.  The thread finds the block
+// Emission with RPT (2 or 4) consecutive rows per thread.  The thread finds the block
 // of its first row by a search of the staged block offsets and splits that
 // row's offset into per-relation digits once; the next rows follow by
 // incrementing the digits like an odometer (rows of a block are ordered
@@ -19,94 +19,108 @@ namespace gj {
 namespace {
 
 // tile_first[t] = block holding the first row of emit tile t (rows
-// [row0 + t*T, ...)); written by the blocks themselves, one scatter pass.
+// [row0 + t*tile_rows, ...)); written by the blocks themselves, one scatter.
 __global__ void k_tile_first(const uint64_t *__restrict__ A, const uint32_t *B_dev, uint64_t row0,
-                             int64_t n, int64_t tiles, uint32_t *tile_first) {
+                             int64_t n, int64_t tiles, int64_t tile_rows, uint32_t *tile_first) {
     const int64_t B = *B_dev;
     for (int64_t b = (int64_t)blockIdx.x * EMIT_DT + threadIdx.x; b < B; b += (int64_t)gridDim.x * EMIT_DT) {
         uint64_t lo = A[b] > row0 ? A[b] - row0 : 0;
         uint64_t hi = (b + 1 < B) ? A[b + 1] - row0 : (uint64_t)n;
-        int64_t t0 = (int64_t)((lo + EMIT4_TILE - 1) / EMIT4_TILE);
-        int64_t t1 = (int64_t)((hi + EMIT4_TILE - 1) / EMIT4_TILE);
+        int64_t t0 = (int64_t)((lo + tile_rows - 1) / tile_rows);
+        int64_t t1 = (int64_t)((hi + tile_rows - 1) / tile_rows);
         for (int64_t t = t0; t < t1 && t < tiles; t++) tile_first[t] = (uint32_t)b;
     }
 }
 
-// Column stores.  A lane holds 4 consecutive rows of a column.  Every store
-// writes whole 32-byte sectors: a 64-bit column stores its 4 values as one
-// 32-byte vector store; a 32-bit column pairs lanes (2m, 2m+1) by shuffle
-// and lane 2m stores the pair's 8 consecutive values as one 32-byte vector
-// store.  Edges of the window (or unaligned buffers) fall back to scalar
-// stores.  Streaming (.cs) stores: the result is not read back here.
-__device__ __forceinline__ void st_cs_v4_b64(unsigned long long *p, const unsigned long long (&v)[EMIT_RPT]) {
+// Column stores.  A lane holds RPT consecutive rows of a column.  Every
+// store writes a whole 32-byte sector: the G = 32 / (RPT * sizeof(T)) lanes
+// of a group pass their values to the group's first lane by shuffle, and
+// that lane writes the group's 32 consecutive bytes with one vector store
+// (v4.b64 or v8.b32).  Edges of the window (or unaligned buffers) fall back
+// to scalar stores.  Streaming (.cs) stores: the result is not read here.
+__device__ __forceinline__ void st_cs_32B(unsigned long long *p, const unsigned long long (&v)[4]) {
     asm volatile("st.global.cs.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(v[0]), "l"(v[1]),
                  "l"(v[2]), "l"(v[3]) : "memory");
 }
 
-__device__ __forceinline__ void st_cs_v8_b32(unsigned int *p, const unsigned int (&a)[EMIT_RPT],
-                                             const unsigned int (&b)[EMIT_RPT]) {
+__device__ __forceinline__ void st_cs_32B(unsigned int *p, const unsigned int (&v)[8]) {
     asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p),
-                 "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "r"(b[2]),
-                 "r"(b[3]) : "memory");
-}
-
-__device__ __forceinline__ void emit_store_col(const unsigned long long (&v)[EMIT_RPT],
-                                               unsigned long long *dst, int64_t rbeg, int nrow,
-                                               bool vec) {
-    if (vec && nrow == EMIT_RPT) {
-        st_cs_v4_b64(dst + rbeg, v);
-    } else {
-#pragma unroll
-        for (int i = 0; i < EMIT_RPT; i++)
-            if (i < nrow) __stcs(dst + rbeg + i, v[i]);
-    }
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                 "r"(v[7]) : "memory");
 }
 
 // all lanes of the warp must call this (shuffles)
-__device__ __forceinline__ void emit_store_col(const unsigned int (&v)[EMIT_RPT], unsigned int *dst,
-                                               int64_t rbeg, int nrow, int pair_rows, bool vec,
-                                               int lane) {
-    unsigned int o[EMIT_RPT];
+template <int RPT, class T>
+__device__ __forceinline__ void emit_store_col(const T (&v)[RPT], T *dst, int64_t rbeg, int nrow,
+                                               int group_rows, bool vec, int lane) {
+    constexpr int PER = 32 / (int)sizeof(T);   // values in one 32-byte store
+    if constexpr (RPT >= PER) {
+        // the lane's own rows fill whole sectors
+        static_assert(RPT % PER == 0, "rows per thread must fill whole sectors");
+        if (vec && nrow == RPT) {
 #pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++) o[i] = __shfl_xor_sync(0xffffffffu, v[i], 1);
-    if (vec && pair_rows == 2 * EMIT_RPT) {
-        if ((lane & 1) == 0) st_cs_v8_b32(dst + rbeg, v, o);
+            for (int s = 0; s < RPT / PER; s++) {
+                T part[PER];
+#pragma unroll
+                for (int i = 0; i < PER; i++) part[i] = v[s * PER + i];
+                st_cs_32B(dst + rbeg + s * PER, part);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+                if (i < nrow) __stcs(dst + rbeg + i, v[i]);
+        }
     } else {
+        constexpr int G = PER / RPT;           // lanes per 32-byte group
+        static_assert(G * RPT == PER, "rows per thread must divide a sector");
+        T all[PER];
 #pragma unroll
-        for (int i = 0; i < EMIT_RPT; i++)
-            if (i < nrow) __stcs(dst + rbeg + i, v[i]);
+        for (int i = 0; i < RPT; i++) all[i] = v[i];
+#pragma unroll
+        for (int k = 1; k < G; k++)
+#pragma unroll
+            for (int i = 0; i < RPT; i++) all[k * RPT + i] = __shfl_down_sync(0xffffffffu, v[i], k);
+        if (vec && group_rows == PER) {
+            if ((lane & (G - 1)) == 0) st_cs_32B(dst + rbeg, all);
+        } else {
+#pragma unroll
+            for (int i = 0; i < RPT; i++)
+                if (i < nrow) __stcs(dst + rbeg + i, v[i]);
+        }
     }
 }
 
-template <int K>
-__global__ void __launch_bounds__(EMIT_DT, (K <= 5 ? 4 : 3))
-k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, const uint32_t *B_dev,
-        uint64_t row0, int64_t n) {
+template <int K, int RPT>
+__global__ void __launch_bounds__(EMIT_DT, (RPT == 8 ? 2 : RPT == 4 ? (K <= 5 ? 4 : 3) : (K <= 5 ? 6 : 4)))
+k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, const uint32_t *B_dev,
+       uint64_t row0, int64_t n) {
+    constexpr int TILE = EMIT_DT * RPT;
     const int64_t B = *B_dev;
-    __shared__ uint64_t s_A[EMIT4_TILE + 1];
+    __shared__ uint64_t s_A[TILE + 1];
     const int64_t tile = blockIdx.x;
-    const int64_t r0 = tile * EMIT4_TILE;
+    const int64_t r0 = tile * TILE;
     if (r0 >= n) return;
-    const int64_t r1 = min(n, r0 + EMIT4_TILE);
+    const int64_t r1 = min(n, r0 + TILE);
     const int64_t first = tile_first[tile];
     const int64_t last = (tile + 1 < tiles) ? (int64_t)tile_first[tile + 1] : B - 1;
     int nb = (int)(last - first + 1);
     // the tile's rows plus the block holding the next tile's first row
-    if (last < first || nb > EMIT4_TILE + 1) {   // cannot happen: every block has >= 1 row
+    if (last < first || nb > TILE + 1) {   // cannot happen: every block has >= 1 row
         if (threadIdx.x == 0) raise_err(e.err, ERRF_BOUNDS);
         return;
     }
     for (int t = threadIdx.x; t < nb; t += EMIT_DT) s_A[t] = e.A[first + t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t rbeg = r0 + (int64_t)threadIdx.x * EMIT_RPT;
+    const int64_t rbeg = r0 + (int64_t)threadIdx.x * RPT;
     // lanes past the end still take part in the warp's shuffles
-    const int nrow = (int)max((int64_t)0, min((int64_t)EMIT_RPT, r1 - rbeg));
-    // rows of the lane pair (2m, 2m+1) that lane 2m would store
-    const int pair_rows = (int)max((int64_t)0, min((int64_t)2 * EMIT_RPT, r1 - (rbeg & ~(int64_t)(2 * EMIT_RPT - 1))));
+    const int nrow = (int)max((int64_t)0, min((int64_t)RPT, r1 - rbeg));
+    // rows of a 32-byte store group of 32-bit and of 64-bit columns
+    const int g32 = (int)max((int64_t)0, min((int64_t)8, r1 - (rbeg & ~(int64_t)7)));
+    const int g64 = (int)max((int64_t)0, min((int64_t)4, r1 - (rbeg & ~(int64_t)3)));
     const uint64_t row = row0 + (uint64_t)rbeg;
     // block of every row: a search for the first, then at most one step per row
-    int lb[EMIT_RPT];
+    int lb[RPT];
     if (nrow > 0) {
         int a = 0, b = nb;
         while (a < b) { int m = (a + b) >> 1; if (s_A[m] <= row) a = m + 1; else b = m; }
@@ -115,7 +129,7 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, con
         lb[0] = 0;
     }
 #pragma unroll
-    for (int i = 1; i < EMIT_RPT; i++) {
+    for (int i = 1; i < RPT; i++) {
         lb[i] = lb[i - 1];
         if (i < nrow && lb[i] + 1 < nb && s_A[lb[i] + 1] <= row + i) lb[i]++;
     }
@@ -123,12 +137,12 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, con
     // all group ids, then all group extents: two rounds of independent loads;
     // a row in the same block as the previous row reuses its values (the
     // load is predicated off, so it costs no memory traffic)
-    bool nb_row[EMIT_RPT];
+    bool nb_row[RPT];
 #pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++) nb_row[i] = (i == 0) || lb[i] != lb[i - 1];
-    uint32_t g[EMIT_RPT][K];
+    for (int i = 0; i < RPT; i++) nb_row[i] = (i == 0) || lb[i] != lb[i - 1];
+    uint32_t g[RPT][K];
 #pragma unroll
-    for (int i = 0; i < EMIT_RPT; i++)
+    for (int i = 0; i < RPT; i++)
 #pragma unroll
         for (int j = 0; j < K; j++)
             g[i][j] = nb_row[i] ? __ldg(e.grp[j] + first + lb[i]) : g[i > 0 ? i - 1 : 0][j];
@@ -138,18 +152,18 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, con
         for (int c = e.col_off[j]; c < e.col_off[j + 1]; c++) {
             if (e.kind[c] != 0) continue;
             const unsigned int *src = (const unsigned int *)e.src[c];
-            unsigned int v[EMIT_RPT];
+            unsigned int v[RPT];
 #pragma unroll
-            for (int i = 0; i < EMIT_RPT; i++)
+            for (int i = 0; i < RPT; i++)
                 v[i] = nb_row[i] ? __ldg(src + g[i][j]) : v[i > 0 ? i - 1 : 0];
-            emit_store_col(v, (unsigned int *)e.dst[c], rbeg, nrow, pair_rows, e.vec, lane);
+            emit_store_col<RPT>(v, (unsigned int *)e.dst[c], rbeg, nrow, g32, e.vec, lane);
         }
     }
-    uint32_t pos[EMIT_RPT][K];
+    uint32_t pos[RPT][K];
     {
-        uint32_t base[EMIT_RPT][K], cnt[EMIT_RPT][K];
+        uint32_t base[RPT][K], cnt[RPT][K];
 #pragma unroll
-        for (int i = 0; i < EMIT_RPT; i++)
+        for (int i = 0; i < RPT; i++)
 #pragma unroll
             for (int j = 0; j < K; j++) {
                 if (nb_row[i]) {
@@ -179,7 +193,7 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, con
 #pragma unroll
         for (int j = 0; j < K; j++) pos[0][j] = base[0][j] + d[j];
 #pragma unroll
-        for (int i = 1; i < EMIT_RPT; i++) {
+        for (int i = 1; i < RPT; i++) {
             if (lb[i] != lb[i - 1]) {
 #pragma unroll
                 for (int j = 0; j < K; j++) d[j] = 0;   // a block starts at digits 0
@@ -204,58 +218,67 @@ k_emit4(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, con
             const int kind = e.kind[c];
             if (kind == 2) {
                 const unsigned long long *src = (const unsigned long long *)e.src[c];
-                unsigned long long v[EMIT_RPT];
+                unsigned long long v[RPT];
 #pragma unroll
-                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(v, (unsigned long long *)e.dst[c], rbeg, nrow, e.vec);
+                for (int i = 0; i < RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                emit_store_col<RPT>(v, (unsigned long long *)e.dst[c], rbeg, nrow, g64, e.vec, lane);
             } else if (kind == 1) {
                 const unsigned int *src = (const unsigned int *)e.src[c];
-                unsigned int v[EMIT_RPT];
+                unsigned int v[RPT];
 #pragma unroll
-                for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(src + pos[i][j]);
-                emit_store_col(v, (unsigned int *)e.dst[c], rbeg, nrow, pair_rows, e.vec, lane);
+                for (int i = 0; i < RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                emit_store_col<RPT>(v, (unsigned int *)e.dst[c], rbeg, nrow, g32, e.vec, lane);
             }
         }
         if (e.rid_out[j]) {
-            unsigned int v[EMIT_RPT];
+            unsigned int v[RPT];
 #pragma unroll
-            for (int i = 0; i < EMIT_RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
-            emit_store_col(v, e.rid_out[j], rbeg, nrow, pair_rows,
-                           e.vec && ((uintptr_t)e.rid_out[j] & 31) == 0, lane);
+            for (int i = 0; i < RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
+            emit_store_col<RPT>(v, e.rid_out[j], rbeg, nrow, g32,
+                                e.vec && ((uintptr_t)e.rid_out[j] & 31) == 0, lane);
         }
     }
 }
 
-template <int K>
+template <int K, int RPT>
 cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0, int64_t n) {
-    const int64_t tiles = ceil_div(n, EMIT4_TILE);
+    constexpr int TILE = EMIT_DT * RPT;
+    const int64_t tiles = ceil_div(n, TILE);
     uint32_t *tile_first = nullptr;
     GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
     // at most one block per row of the window
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, EMIT_DT), (int64_t)c.num_sms * 16));
-    k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, tile_first); c.launches++;
+    k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, TILE, tile_first); c.launches++;
     if (c.prof) cudaEventRecord(c.event(), c.stream);
-    k_emit4<K><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, tile_first, tiles, B_dev, row0, n); c.launches++;
+    k_emit<K, RPT><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, tile_first, tiles, B_dev, row0, n); c.launches++;
     cudaError_t e = cudaGetLastError();
     dfree(c, tile_first);
     return e;
+}
+
+template <int RPT>
+cudaError_t launch_rpt(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
+                       int64_t n) {
+    switch (k) {
+        case 1: return launch_k<1, RPT>(c, s, B_dev, row0, n);
+        case 2: return launch_k<2, RPT>(c, s, B_dev, row0, n);
+        case 3: return launch_k<3, RPT>(c, s, B_dev, row0, n);
+        case 4: return launch_k<4, RPT>(c, s, B_dev, row0, n);
+        case 5: return launch_k<5, RPT>(c, s, B_dev, row0, n);
+        case 6: return launch_k<6, RPT>(c, s, B_dev, row0, n);
+        case 7: return launch_k<7, RPT>(c, s, B_dev, row0, n);
+        case 8: return launch_k<8, RPT>(c, s, B_dev, row0, n);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
                         int64_t n) {
-    switch (k) {
-        case 1: return launch_k<1>(c, s, B_dev, row0, n);
-        case 2: return launch_k<2>(c, s, B_dev, row0, n);
-        case 3: return launch_k<3>(c, s, B_dev, row0, n);
-        case 4: return launch_k<4>(c, s, B_dev, row0, n);
-        case 5: return launch_k<5>(c, s, B_dev, row0, n);
-        case 6: return launch_k<6>(c, s, B_dev, row0, n);
-        case 7: return launch_k<7>(c, s, B_dev, row0, n);
-        case 8: return launch_k<8>(c, s, B_dev, row0, n);
-    }
-    return cudaErrorInvalidValue;
+    if (c.emit_rpt == 2) return launch_rpt<2>(c, k, s, B_dev, row0, n);
+    if (c.emit_rpt == 8) return launch_rpt<8>(c, k, s, B_dev, row0, n);
+    return launch_rpt<4>(c, k, s, B_dev, row0, n);
 }
 
 }  // namespace gj

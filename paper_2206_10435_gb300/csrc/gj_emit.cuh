@@ -9,8 +9,6 @@ constexpr int EMIT_DT = 256;
 constexpr int EMIT_MAXR = MAX_REL;
 constexpr int EMIT_MAXV = 32;
 constexpr int EMIT_MAXP = 32;
-constexpr int EMIT_RPT = 4;
-constexpr int EMIT4_TILE = EMIT_DT * EMIT_RPT;
 constexpr int MAXC = EMIT_MAXV + EMIT_MAXP;
 
 struct Emit4Spec {

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "gj.h")
 GJ_OK, GJ_ERR_INVALID, GJ_ERR_NOT_ACYCLIC, GJ_ERR_OOM, GJ_ERR_OVERFLOW, GJ_ERR_CUDA, \
     GJ_ERR_TIMEOUT, GJ_ERR_STATE, GJ_ERR_CAPACITY = range(9)
 GJ_REL_BORROW, GJ_REL_COPY, GJ_REL_HOST = 0, 1, 2
+GJ_OPT_EMIT_ROWS_PER_THREAD = 1
 SAT = (1 << 64) - 1
 
 
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "gj_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P]),
         "gj_destroy": (None, [_P]),
         "gj_set_stream": (ctypes.c_int, [_P, _P]),
+        "gj_set_option": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
         "gj_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Profile)]),
         "gj_load_relation": (ctypes.c_int, [_P, ctypes.POINTER(RelationDesc),
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -192,6 +194,9 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_option(self, option: int, value: int):
+        _check(lib().gj_set_option(self.h, option, value), "gj_set_option")
 
     def profile(self, enable: bool = True) -> dict:
         """Counters since the last call (synchronises), then profiling on/off."""
