@@ -150,7 +150,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-EMIT_PROFILE = os.path.join(ROOT, "profiles", "k_emit4_chain5_zipf.md")
+EMIT_PROFILE = os.path.join(ROOT, "profiles", "k_emit_chain5_zipf.md")
 EMIT_SOURCE = os.path.join(ROOT, "paper_2206_10435_gb300", "csrc", "gj_emit.cu")
 
 
@@ -350,7 +350,7 @@ def main():
     tpr, tnote = emit_traffic_per_row() if a.workload == "chain5_zipf" else (None, "captured for chain5_zipf only")
     rows_per_launch = prof["emit_rows"] / max(prof["emit_launches"], 1)
     traffic = tpr * rows_per_launch if tpr is not None else None
-    roofline = {"bound": "hbm", "kernel": "k_emit4 (desummarise emit)",
+    roofline = {"bound": "hbm", "kernel": "k_emit<K=5,RPT=4> (desummarise emit)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "traffic_note": tnote,
