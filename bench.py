@@ -680,22 +680,21 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
         ids0 = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
         qq0 = ctx.query(ids0)
         qq0.summarize()
-        dbuf = qq0.alloc_columns(CH)
-        hbuf = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in dbuf]
+        # result chunks go straight into pinned host columns: the emit kernel
+        # stores them over the host link (no device staging buffer, no copy)
+        hbuf = [torch.empty(CH, dtype=torch.int32 if w == 4 else torch.int64, pin_memory=True)
+                for w in qq0.col_width]
         qq0.close()
         for i in ids0:
             ctx.release_relation(i)
-        row_bytes = sum(t.element_size() for t in dbuf)
+        row_bytes = sum(t.element_size() for t in hbuf)
 
         def one():
             ids = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
             qq = ctx.query(ids)
             tot = qq.summarize()
             for r0 in range(0, tot, CH):
-                cols = qq.desummarize(r0, CH, out=dbuf)
-                m = cols[0].shape[0]
-                for h, d in zip(hbuf, cols):
-                    h[:m].copy_(d, non_blocking=True)
+                qq.desummarize(r0, CH, out=hbuf)
             stream.synchronize()
             qq.close()
             for i in ids:
@@ -714,8 +713,9 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
     d2h = tot * row_bytes
     return {"value": tot * a.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
-            "chunk_rows": CH, "note": "relations H2D from pinned host memory, every result "
-                                      "chunk D2H into pinned host memory, inside the timed region"}
+            "chunk_rows": CH, "note": "relations H2D from pinned host memory; every result chunk "
+                                      "written by the emit kernel straight into pinned host "
+                                      "memory over the host link; all inside the timed region"}
 
 
 if __name__ == "__main__":

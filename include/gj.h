@@ -230,11 +230,18 @@ gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
 
 /*
  * Desummarisation (Section 3.6): writes result rows [row0, row0 + n_rows)
- * (clipped to |Q|) into caller-owned device columns out_cols[0..n_cols-1]
+ * (clipped to |Q|) into caller-owned columns out_cols[0..n_cols-1]
  * (layout from gj_query_sizes: the V key columns as int32, then payloads).
- * If rowid_cols is non-NULL, rowid_cols[j] (device uint32[n_rows], may be
- * NULL per relation) receives the row id r_j of every result row.
- * *n_out receives the number of rows written.  Requires gj_summarize.
+ * If rowid_cols is non-NULL, rowid_cols[j] (uint32[n_rows], may be NULL per
+ * relation) receives the row id r_j of every result row.
+ * Every column is either device memory of the context's device (or managed
+ * memory) or pinned host memory the device can address (cudaHostAlloc,
+ * cudaHostRegister; torch pin_memory()): the emit kernel then stores the
+ * rows straight into host memory over the host link, without a device
+ * staging buffer or a copy.  Pageable host memory is rejected
+ * (GJ_ERR_INVALID).  *n_out receives the number of rows written; the rows
+ * are in place once the context's stream reaches this point (the call
+ * synchronises it).  Requires gj_summarize.
  */
 gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
                          void *const *out_cols, uint32_t *const *rowid_cols, uint64_t *n_out);

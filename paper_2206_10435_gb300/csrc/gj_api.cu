@@ -517,8 +517,36 @@ gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows, i
 gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows, void *const *out_cols,
                          uint32_t *const *rowid_cols, uint64_t *n_out) {
     if (!q || !n_out) return GJ_ERR_INVALID;
-    DeviceGuard g(q->s.cs->c.device);
-    return desummarize(q->s, row0, n_rows, out_cols, rowid_cols, n_out);
+    *n_out = 0;
+    if (!out_cols) return GJ_ERR_INVALID;
+    const int device = q->s.cs->c.device;
+    DeviceGuard g(device);
+    // every column must be addressable by the device: its own memory,
+    // managed memory, or pinned host memory (translated to the device's
+    // address for it)
+    auto device_view = [&](void *p, void **dv) -> bool {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+        if (at.type == cudaMemoryTypeDevice) { *dv = p; return at.device == device; }
+        if (at.type == cudaMemoryTypeManaged) { *dv = p; return true; }
+        if (at.type == cudaMemoryTypeHost && at.devicePointer) { *dv = at.devicePointer; return true; }
+        return false;
+    };
+    const size_t ncols = q->s.var_rel.size() + q->s.col_rel.size();
+    std::vector<void *> cols(ncols);
+    for (size_t i = 0; i < ncols; i++)
+        if (!out_cols[i] || !device_view(out_cols[i], &cols[i])) return GJ_ERR_INVALID;
+    std::vector<uint32_t *> rids;
+    if (rowid_cols) {
+        rids.assign(q->s.k, nullptr);
+        for (int j = 0; j < q->s.k; j++) {
+            if (!rowid_cols[j]) continue;
+            void *dv = nullptr;
+            if (!device_view(rowid_cols[j], &dv)) return GJ_ERR_INVALID;
+            rids[j] = (uint32_t *)dv;
+        }
+    }
+    return desummarize(q->s, row0, n_rows, cols.data(), rowid_cols ? rids.data() : nullptr, n_out);
 }
 
 }  // extern "C"

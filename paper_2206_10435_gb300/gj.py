@@ -351,7 +351,9 @@ class Query:
 
     def desummarize(self, row0: int, n_rows: int, out=None, rowids: bool = False):
         """Result rows [row0, row0+n_rows) as columns (V keys, then payloads);
-        with rowids=True also the row id of every relation."""
+        with rowids=True also the row id of every relation.  `out` may be
+        device tensors or pinned host tensors (pin_memory): the kernel then
+        writes the rows straight into host memory."""
         torch = self.ctx.torch
         if out is None:
             out = self.alloc_columns(n_rows)

@@ -120,3 +120,38 @@ def test_offsets_past_2_32_inside_one_block(kctx, k, rows):
             got = cols[k + 1 + j].cpu().numpy()
             assert np.array_equal(got, q.relations[j].payloads[0][want[j].astype(np.int64)]), j
     run.close()
+
+
+def test_pinned_host_columns(kctx):
+    """Rows written straight into pinned host memory equal the device rows."""
+    q = one_payload(G.random_tree_query(1207, 4, max_rows=60, domain=6, max_new=2,
+                                        min_rows=20), "i64")
+    run = Run(kctx, q)
+    total = run.summarize()
+    for r0, n in [(0, total), (1023, 4099)]:
+        dev_cols, _ = run.q.desummarize(r0, n, rowids=True)
+        host = [torch.empty(n, dtype=c.dtype, pin_memory=True) for c in dev_cols]
+        got = run.q.desummarize(r0, n, out=host)
+        for a, b in zip(dev_cols, got):
+            assert not b.is_cuda
+            assert torch.equal(a.cpu(), b)
+    run.close()
+
+
+def test_pageable_columns_rejected(kctx):
+    from paper_2206_10435_gb300 import gj
+    q = one_payload(G.random_tree_query(1207, 4, max_rows=60, domain=6, max_new=2,
+                                        min_rows=20), "i64")
+    run = Run(kctx, q)
+    total = run.summarize()
+    dev_cols, _ = run.q.desummarize(0, 10, rowids=True)
+    pageable = [torch.empty(10, dtype=c.dtype) for c in dev_cols]
+    with pytest.raises(gj.GJError) as ei:
+        run.q.desummarize(0, 10, out=pageable)
+    assert ei.value.status == gj.GJ_ERR_INVALID
+    # the context still works
+    again, _ = run.q.desummarize(0, 10, rowids=True)
+    for a, b in zip(dev_cols, again):
+        assert torch.equal(a, b)
+    assert total > 0
+    run.close()
