@@ -140,6 +140,12 @@ struct ExpandOut {
     uint32_t *grp[MAXR];
     uint32_t *lh;
     uint64_t *unit;
+    // last level of a desummarisation: tile_first[t] = block holding window
+    // row t * tile_rows (the emit's tile map), written by the blocks
+    uint32_t *tile_first;
+    int64_t tile_rows, tiles;
+    uint64_t row0;
+    int64_t n;
 };
 
 // slot_first[t] = item owning output slot t*EXP_TILE (items own the slots
@@ -188,8 +194,18 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             const uint32_t h = lo_in[i] + (uint32_t)(slot - s_off[a - 1]);
             const uint32_t g = s.lgid[h];
             const uint64_t unit = unit_in[i];
-            o.A[slot] = s.A[i] + unit * s.loff[h];
-            if (o.W) o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
+            const uint64_t A = s.A[i] + unit * s.loff[h];
+            o.A[slot] = A;
+            const uint64_t W = (o.W || o.tile_first) ? s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]) : 0;
+            if (o.W) o.W[slot] = W;
+            if (o.tile_first) {
+                // the block's rows [A, A + W) inside the window, as tiles
+                const uint64_t lo = A > o.row0 ? A - o.row0 : 0;
+                const uint64_t hi = min(A + W - o.row0, (uint64_t)o.n);
+                const int64_t T = o.tile_rows;
+                for (int64_t t = (int64_t)((lo + T - 1) / T); t < o.tiles && (uint64_t)(t * T) < hi; t++)
+                    o.tile_first[t] = (uint32_t)slot;
+            }
             for (int p = 0; p < j; p++) o.grp[p][slot] = s.grp[p][i];
             o.grp[j][slot] = g;
             if (o.lh) o.lh[slot] = h;
@@ -280,9 +296,15 @@ cudaError_t frontier_alloc(Ctx &c, Frontier &f, int64_t cap, int depth, bool kee
 // overlap result rows [row0, row_end).  No host synchronisation: every
 // frontier holds at most one item per row of the window, so arrays are
 // sized by the window and item counts stay in device memory.
-// keep_last: also fill lh and unit.
+// keep_last: also fill lh and unit.  tm: the last level also writes the emit
+// kernel's tile map (the block holding the first row of every emit tile).
+struct TileMap {
+    uint32_t *tile_first;   // [tiles + 1]
+    int64_t tile_rows, tiles;
+};
+
 cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bool keep_last,
-                   Frontier &out) {
+                   Frontier &out, const TileMap *tm = nullptr) {
     Ctx &c = q.ctx();
     const QRel &root = q.r[q.pre[0]];
     const int64_t cap = (int64_t)(row_end - row0);
@@ -346,6 +368,13 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         for (int p = 0; p <= j; p++) o.grp[p] = nxt.grp[p];
         o.lh = nxt.lh;
         o.unit = nxt.unit;
+        if (last && tm) {
+            o.tile_first = tm->tile_first;
+            o.tile_rows = tm->tile_rows;
+            o.tiles = tm->tiles;
+            o.row0 = row0;
+            o.n = (int64_t)(row_end - row0);
+        }
         k_slot_first<<<grid_for(c, cap), DT, 0, c.stream>>>(excl, cnt, cur.F_dev, slot_first); c.launches++;
         k_expand_write<<<pgrid, DT, 0, c.stream>>>(s, cur.F_dev, excl, nxt.F_dev, slot_first, lo,
                                                    unit, o); c.launches++;
@@ -522,7 +551,15 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
     if (!out_cols) return GJ_ERR_INVALID;
     Frontier f;
     if (c.prof) cudaEventRecord(c.event(true), c.stream);
-    cudaError_t e = expand(q, row0, row0 + n, q.k, false, f);
+    // with two or more relations the last expansion level writes the emit
+    // kernel's tile map itself
+    TileMap tm{};
+    if (q.k >= 2 && q.k <= 8) {
+        tm.tile_rows = (int64_t)EMIT_DT * c.emit_rpt;
+        tm.tiles = ceil_div((int64_t)n, tm.tile_rows);
+        if (dalloc(c, &tm.tile_first, tm.tiles + 1) != cudaSuccess) return GJ_ERR_OOM;
+    }
+    cudaError_t e = expand(q, row0, row0 + n, q.k, false, f, tm.tile_first ? &tm : nullptr);
     if (c.prof) cudaEventRecord(c.event(true), c.stream);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
     uint64_t width = 0;
@@ -561,7 +598,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
         s.vec = vec;
         s.A = f.A;
         s.err = c.err;
-        e = launch_emit(c, q.k, s, f.F_dev, row0, (int64_t)n);
+        e = launch_emit(c, q.k, s, f.F_dev, row0, (int64_t)n, tm.tile_first);
     } else {
         EmitSpec s{};
         s.k = q.k;
@@ -599,6 +636,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
         c.emit_bytes += n * width;
     }
     frontier_free(c, f);
+    dfree(c, tm.tile_first);
     if (e != cudaSuccess) return GJ_ERR_CUDA;
     gj_status st = check_device_error(c);
     if (st != GJ_OK) return st;

@@ -241,16 +241,19 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
 }
 
 template <int K, int RPT>
-cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0, int64_t n) {
+cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0, int64_t n,
+                     const uint32_t *pre) {
     constexpr int TILE = EMIT_DT * RPT;
     const int64_t tiles = ceil_div(n, TILE);
     uint32_t *tile_first = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
-    // at most one block per row of the window
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, EMIT_DT), (int64_t)c.num_sms * 16));
-    k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, TILE, tile_first); c.launches++;
+    if (!pre) {
+        GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
+        // at most one block per row of the window
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, EMIT_DT), (int64_t)c.num_sms * 16));
+        k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, TILE, tile_first); c.launches++;
+    }
     if (c.prof) cudaEventRecord(c.event(), c.stream);
-    k_emit<K, RPT><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, tile_first, tiles, B_dev, row0, n); c.launches++;
+    k_emit<K, RPT><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, pre ? pre : tile_first, tiles, B_dev, row0, n); c.launches++;
     cudaError_t e = cudaGetLastError();
     dfree(c, tile_first);
     return e;
@@ -258,16 +261,16 @@ cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t
 
 template <int RPT>
 cudaError_t launch_rpt(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
-                       int64_t n) {
+                       int64_t n, const uint32_t *pre) {
     switch (k) {
-        case 1: return launch_k<1, RPT>(c, s, B_dev, row0, n);
-        case 2: return launch_k<2, RPT>(c, s, B_dev, row0, n);
-        case 3: return launch_k<3, RPT>(c, s, B_dev, row0, n);
-        case 4: return launch_k<4, RPT>(c, s, B_dev, row0, n);
-        case 5: return launch_k<5, RPT>(c, s, B_dev, row0, n);
-        case 6: return launch_k<6, RPT>(c, s, B_dev, row0, n);
-        case 7: return launch_k<7, RPT>(c, s, B_dev, row0, n);
-        case 8: return launch_k<8, RPT>(c, s, B_dev, row0, n);
+        case 1: return launch_k<1, RPT>(c, s, B_dev, row0, n, pre);
+        case 2: return launch_k<2, RPT>(c, s, B_dev, row0, n, pre);
+        case 3: return launch_k<3, RPT>(c, s, B_dev, row0, n, pre);
+        case 4: return launch_k<4, RPT>(c, s, B_dev, row0, n, pre);
+        case 5: return launch_k<5, RPT>(c, s, B_dev, row0, n, pre);
+        case 6: return launch_k<6, RPT>(c, s, B_dev, row0, n, pre);
+        case 7: return launch_k<7, RPT>(c, s, B_dev, row0, n, pre);
+        case 8: return launch_k<8, RPT>(c, s, B_dev, row0, n, pre);
     }
     return cudaErrorInvalidValue;
 }
@@ -275,10 +278,10 @@ cudaError_t launch_rpt(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev,
 }  // namespace
 
 cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
-                        int64_t n) {
-    if (c.emit_rpt == 2) return launch_rpt<2>(c, k, s, B_dev, row0, n);
-    if (c.emit_rpt == 8) return launch_rpt<8>(c, k, s, B_dev, row0, n);
-    return launch_rpt<4>(c, k, s, B_dev, row0, n);
+                        int64_t n, const uint32_t *tile_first) {
+    if (c.emit_rpt == 2) return launch_rpt<2>(c, k, s, B_dev, row0, n, tile_first);
+    if (c.emit_rpt == 8) return launch_rpt<8>(c, k, s, B_dev, row0, n, tile_first);
+    return launch_rpt<4>(c, k, s, B_dev, row0, n, tile_first);
 }
 
 }  // namespace gj
