@@ -170,6 +170,8 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
                const uint32_t *__restrict__ lo_in, const uint64_t *__restrict__ unit_in,
                ExpandOut o) {
     __shared__ uint32_t s_off[EXP_TILE + 1];
+    __shared__ uint64_t s_A[EXP_TILE];   // tile map only: first rows of the tile's blocks
+    __shared__ uint64_t s_end;            // and the end of its last block
     const int64_t F = *F_dev, Fout = *Fout_dev;
     const int64_t tiles = (Fout + EXP_TILE - 1) / EXP_TILE;
     const int j = s.depth;
@@ -196,20 +198,31 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             const uint64_t unit = unit_in[i];
             const uint64_t A = s.A[i] + unit * s.loff[h];
             o.A[slot] = A;
-            const uint64_t W = (o.W || o.tile_first) ? s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]) : 0;
-            if (o.W) o.W[slot] = W;
+            if (o.W) o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
             if (o.tile_first) {
-                // the block's rows [A, A + W) inside the window, as tiles
-                const uint64_t lo = A > o.row0 ? A - o.row0 : 0;
-                const uint64_t hi = min(A + W - o.row0, (uint64_t)o.n);
-                const int64_t T = o.tile_rows;
-                for (int64_t t = (int64_t)((lo + T - 1) / T); t < o.tiles && (uint64_t)(t * T) < hi; t++)
-                    o.tile_first[t] = (uint32_t)slot;
+                s_A[slot - o0] = A;
+                // the tile's last block ends where the next tile starts: its
+                // size is needed
+                if (slot == o1 - 1) s_end = A + s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
             }
             for (int p = 0; p < j; p++) o.grp[p][slot] = s.grp[p][i];
             o.grp[j][slot] = g;
             if (o.lh) o.lh[slot] = h;
             if (o.unit) o.unit[slot] = unit;
+        }
+        if (o.tile_first) {
+            // block `slot` holds rows [A, next block's A) of the result: the
+            // emit tiles whose first row lies there point at it
+            __syncthreads();
+            const int64_t T = o.tile_rows;
+            for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
+                const uint64_t A = s_A[slot - o0];
+                const uint64_t end = slot + 1 < o1 ? s_A[slot + 1 - o0] : s_end;
+                const uint64_t lo = A > o.row0 ? A - o.row0 : 0;
+                const uint64_t hi = min(end - o.row0, (uint64_t)o.n);
+                for (int64_t t = (int64_t)((lo + T - 1) / T); t < o.tiles && (uint64_t)(t * T) < hi; t++)
+                    o.tile_first[t] = (uint32_t)slot;
+            }
         }
     }
 }
