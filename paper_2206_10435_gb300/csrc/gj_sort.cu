@@ -146,18 +146,21 @@ k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
         atomicExch(&st[d], (unsigned long long)(ST_PREFIX | (excl + cnt)));
         s_glob[d] = bucket_base[d] + (uint32_t)excl;
     }
-    // tile-local exclusive offsets over digits
-    s_tile_off[d] = cnt;
-    __syncthreads();
+    // tile-local exclusive offsets over digits: a shuffle scan per warp of
+    // 32 digits, then the totals of the preceding warps (s_misc holds them;
+    // the tile id it held is in a register by now)
     {
-        // 256-wide inclusive scan in shared memory (Hillis-Steele)
-        for (int off = 1; off < RS_RADIX; off <<= 1) {
-            uint32_t t = d >= off ? s_tile_off[d - off] : 0u;
-            __syncthreads();
-            s_tile_off[d] += t;
-            __syncthreads();
+        uint32_t x = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
         }
-        s_tile_off[d] -= cnt;
+        if (lane == 31) s_misc[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; w++) pre += s_misc[w];
+        s_tile_off[d] = pre + x - cnt;
     }
     __syncthreads();
     // stage in digit order
