@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--rows", type=int, default=10**7)
     p.add_argument("--domain", type=int, default=10**6)
     p.add_argument("--zipf", type=float, default=1.1)
+    p.add_argument("--drop-attrs", default="",
+                   help="comma-separated attribute ids projected away early (Section 3.7); "
+                        "each must be held by one relation, e.g. 0,5 for the 5-chain's ends")
     p.add_argument("--chunk-log2", type=int, default=28)
     p.add_argument("--emit-rpt", type=int, default=4, choices=[2, 4, 8],
                    help="result rows per thread of the emit kernel")
@@ -66,14 +69,23 @@ def workload_name(a):
     if a.workload == "chain3_uniform":
         return ("chain3_uniform: R1(A,B) R2(B,C) R3(C,D), 10^4 rows/table, int32 keys, A,D "
                 "uniform over [0,10^4), B,C uniform over [0,1000), int32 payload/table, "
-                f"desummarised in 2^{a.chunk_log2}-row chunks")
+                f"desummarised in 2^{a.chunk_log2}-row chunks" + drop_note(a))
     if a.workload == "star_poisson":
         return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
                 "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     return (f"chain5_zipf: 5-table chain R_i(K_i-1,K_i), {a.rows} rows/table, int32 keys "
             f"Zipf({a.zipf}) over [0,{a.domain}), int64 payload/table, "
-            f"desummarised in 2^{a.chunk_log2}-row chunks")
+            f"desummarised in 2^{a.chunk_log2}-row chunks" + drop_note(a))
+
+
+def drop_list(a):
+    return [int(x) for x in a.drop_attrs.split(",") if x.strip()]
+
+
+def drop_note(a):
+    d = drop_list(a)
+    return f"; attributes {d} projected away early (Section 3.7)" if d else ""
 
 
 def make_query(a, rank):
@@ -177,7 +189,7 @@ def emit_traffic_per_row():
         return None, "no traffic in the ncu summary"
 
 
-def cpu_baseline(a, q_full, sample_rows):
+def cpu_baseline(a, q_full, sample_rows, drop=()):
     """The oracle, as it stands, on a bounded sample: the same tables with
     the root restricted to its first `sample_rows` rows (a sub-join of the
     workload); cascade of hash joins + canonical sort + column materialisation
@@ -190,8 +202,8 @@ def cpu_baseline(a, q_full, sample_rows):
                      [p[:sample_rows].copy() for p in R1.payloads])
     qs = G.Query("sample", [sub] + q_full.relations[1:], q_full.attr_names)
     t0 = time.perf_counter()
-    j = O.join(qs, max_tuples=400_000_000)
-    cols = O.columns(qs, j.rowids)
+    j = O.join(qs, max_tuples=400_000_000, drop=drop)
+    cols = O.columns(qs, j.rowids, drop)
     dt = time.perf_counter() - t0
     n = int(j.rowids.shape[0])
     del cols
@@ -207,10 +219,10 @@ def run_reference(a, rank, world):
         return
     q = make_query(a, 0)
     for _ in range(a.warmup):
-        cpu_baseline(a, q, a.cpu_sample_rows // 4)
+        cpu_baseline(a, q, a.cpu_sample_rows // 4, drop_list(a))
     vals, secs, tuples = [], 0.0, 0
     for _ in range(a.steps):
-        r = cpu_baseline(a, q, a.cpu_sample_rows // 4)
+        r = cpu_baseline(a, q, a.cpu_sample_rows // 4, drop_list(a))
         secs += r["seconds"]
         tuples += r["tuples"]
     value = tuples / secs
@@ -291,7 +303,7 @@ def main():
         if record:
             ev[0].record(stream)
         ids = [ctx.load_relation(ks, attrs, ps) for ks, ps, attrs in rels]
-        qq = ctx.query(ids)                       # factor construction
+        qq = ctx.query(ids, drop_attrs=drop_list(a))   # factor construction
         if record:
             ev[1].record(stream)
         total = qq.summarize()                    # upward + downward passes
@@ -347,7 +359,7 @@ def main():
 
     peak, peak_kind = measured_peaks()
     achieved = (prof["emit_bytes"] / (prof["emit_ms"] * 1e6)) if prof["emit_ms"] else None
-    tpr, tnote = emit_traffic_per_row() if a.workload == "chain5_zipf" else (None, "captured for chain5_zipf only")
+    tpr, tnote = emit_traffic_per_row() if a.workload == "chain5_zipf" and not drop_list(a) else (None, "captured for chain5_zipf (all columns) only")
     rows_per_launch = prof["emit_rows"] / max(prof["emit_launches"], 1)
     traffic = tpr * rows_per_launch if tpr is not None else None
     roofline = {"bound": "hbm", "kernel": "k_emit<K=5,RPT=4> (desummarise emit)",
@@ -361,7 +373,7 @@ def main():
                 "emit_ms_per_step": prof["emit_ms"] / a.steps}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline(a, q, a.cpu_sample_rows)
+        cpu = cpu_baseline(a, q, a.cpu_sample_rows, drop_list(a))
         cpu.pop("seconds")
         cpu.pop("tuples")
     if rank == 0:
@@ -678,7 +690,7 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
     d2h = 0
     with torch.cuda.stream(stream):
         ids0 = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
-        qq0 = ctx.query(ids0)
+        qq0 = ctx.query(ids0, drop_attrs=drop_list(a))
         qq0.summarize()
         # result chunks go straight into pinned host columns: the emit kernel
         # stores them over the host link (no device staging buffer, no copy)
@@ -691,7 +703,7 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
 
         def one():
             ids = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
-            qq = ctx.query(ids)
+            qq = ctx.query(ids, drop_attrs=drop_list(a))
             tot = qq.summarize()
             for r0 in range(0, tot, CH):
                 qq.desummarize(r0, CH, out=hbuf)

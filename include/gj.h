@@ -177,6 +177,24 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
  * Builds any factor it needs.
  */
 gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out);
+
+/*
+ * Early projection (Section 3.7): gj_query_create for a result without the
+ * attributes drop_attrs[0..n_drop-1].  Those variables are deleted from the
+ * model before the summary is built: V omits them, gj_desummarize writes no
+ * column for them and the rows are ordered by the remaining variables of V,
+ * ties broken by the row ids r_1..r_k.  The result keeps bag semantics: it
+ * holds the same |Q| row-id tuples as the full join, only without the
+ * dropped columns and in that order.
+ * Supported: attributes that occur in exactly one relation of the query.
+ * That relation's factor groups its rows by its remaining key columns, so
+ * it has fewer groups and the summary shrinks.  A join attribute (shared by
+ * two relations; deleting it needs the potential join of Algorithm 1), an
+ * attribute no relation holds, or a root left without key columns gives
+ * GJ_ERR_INVALID.
+ */
+gj_status gj_query_create_projected(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
+                                    const int32_t *drop_attrs, int32_t n_drop, gj_query **out);
 void gj_query_destroy(gj_query *q);
 gj_status gj_query_sizes(gj_query *q, gj_query_sizes_t *out);
 

@@ -27,6 +27,11 @@ Readings of the paper that this oracle fixes:
   do not exist (Section 3.3: entries below 1 are dropped).
 * Counts are exact below 2^64 - 1; that value marks a clamped count, and a
   join whose size reaches it is reported as overflowing.
+* Early projection (Section 3.7): a dropped attribute is deleted from V.
+  The result is the same bag of row-id tuples, its columns are the
+  remaining V attributes and the payloads, and its rows are ordered by the
+  remaining V values, then the row ids.  Only attributes held by exactly
+  one relation can be dropped (a shared one would need the potential join).
 """
 from __future__ import annotations
 
@@ -99,8 +104,12 @@ class Plan:
     var_col: list      # its column there
 
 
-def plan(query) -> Plan:
+def plan(query, drop=()) -> Plan:
     rels = query.relations
+    drop = set(drop)
+    for a in drop:
+        if sum(R.attrs.count(a) for R in rels) != 1:
+            raise ValueError(f"attribute {a} is not held by exactly one relation")
     k = len(rels)
     parent, sep = [-1], [[]]
     seen = set(rels[0].attrs) if k else set()
@@ -123,7 +132,7 @@ def plan(query) -> Plan:
     V, var_rel, var_col = [], [], []
     for t in order:
         for c, a in enumerate(rels[t].attrs):
-            if a not in V:
+            if a not in V and a not in drop:
                 V.append(a)
                 var_rel.append(t)
                 var_col.append(c)
@@ -208,10 +217,11 @@ class Joined:
     intermediate: list         # size of the cascade after joining 0..j
 
 
-def join(query, max_tuples: int = 50_000_000) -> Joined:
-    """Materialise the join (cascade of hash joins + canonical sort)."""
+def join(query, max_tuples: int = 50_000_000, drop=()) -> Joined:
+    """Materialise the join (cascade of hash joins + canonical sort, by the
+    V of the projection when attributes are dropped)."""
     lib = _load()
-    pl = plan(query)
+    pl = plan(query, drop)
     m = _Marshal(query, pl)
     k = len(query.relations)
     c = count(query)
@@ -230,10 +240,10 @@ def join(query, max_tuples: int = 50_000_000) -> Joined:
     return Joined(out[:n], [int(x) for x in inter])
 
 
-def columns(query, rowids: np.ndarray) -> list:
+def columns(query, rowids: np.ndarray, drop=()) -> list:
     """Materialised columns: the V attributes (int32), then every
     relation's payloads in relation order (Section 3.6: the flat result)."""
-    pl = plan(query)
+    pl = plan(query, drop)
     cols = []
     for t, c in zip(pl.var_rel, pl.var_col):
         cols.append(query.relations[t].keys[c][rowids[:, t]])
@@ -250,12 +260,12 @@ class Level:
     offset: np.ndarray         # uint64 first result row of the run
 
 
-def gfjs_levels(query, rowids: np.ndarray) -> list:
+def gfjs_levels(query, rowids: np.ndarray, drop=()) -> list:
     """Summary levels of the canonically ordered result: level l holds one
     run per distinct prefix (v_0..v_l) (Def. 1, Algorithm 4)."""
-    pl = plan(query)
+    pl = plan(query, drop)
     n = rowids.shape[0]
-    vcols = columns(query, rowids)[:len(pl.V)]
+    vcols = columns(query, rowids, drop)[:len(pl.V)]
     levels = []
     change = np.zeros(n, dtype=bool)
     if n:

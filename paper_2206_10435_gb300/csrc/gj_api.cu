@@ -341,11 +341,32 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
     return from_cuda(cudaStreamSynchronize(c.stream));
 }
 
-gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out) {
+}  // extern "C"
+
+namespace {
+
+// Plans a query over the relations rel_ids (the first is the root) and gets
+// every relation's factor.  Attributes in `drop` are left out of the result
+// (early projection, Section 3.7): each must occur in exactly one relation,
+// which then groups its rows by its remaining key columns.
+gj_status query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
+                       const std::set<int32_t> &drop, gj_query **out) {
     if (!ctx) return GJ_ERR_INVALID;
     std::lock_guard<std::recursive_mutex> lock(ctx->s.mu);
     if (!ctx || !rel_ids || !out || n_rel < 1 || n_rel > MAX_REL) return GJ_ERR_INVALID;
     *out = nullptr;
+    for (int32_t a : drop) {
+        int holders = 0;
+        for (int j = 0; j < n_rel; j++) {
+            auto it = ctx->s.rels.find(rel_ids[j]);
+            if (it == ctx->s.rels.end()) return GJ_ERR_INVALID;
+            const std::vector<int32_t> &attr = it->second->attr;
+            holders += (int)std::count(attr.begin(), attr.end(), a);
+        }
+        // a join attribute would need the potential join of the relations
+        // sharing it; an attribute nobody holds is a caller error
+        if (holders != 1) return GJ_ERR_INVALID;
+    }
     std::unique_ptr<gj_query> qq(new gj_query());
     QueryState &q = qq->s;
     q.cs = &ctx->s;
@@ -360,12 +381,14 @@ gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj
         t.R = it->second.get();
         const std::vector<int32_t> &attr = t.R->attr;
         if (j == 0) {
-            for (int c = 0; c < t.R->nk; c++) t.new_cols.push_back(c);
+            for (int c = 0; c < t.R->nk; c++)
+                if (!drop.count(attr[c])) t.new_cols.push_back(c);
+            if (t.new_cols.empty()) return GJ_ERR_INVALID;   // nothing left to group by
         } else {
             std::vector<int32_t> shared;
             for (int c = 0; c < t.R->nk; c++) {
                 if (seen.count(attr[c])) { shared.push_back(attr[c]); t.sep_cols.push_back(c); }
-                else t.new_cols.push_back(c);
+                else if (!drop.count(attr[c])) t.new_cols.push_back(c);
             }
             if (shared.empty()) return GJ_ERR_INVALID;   // a cross product, not an equi-join
             int parent = -1;
@@ -412,6 +435,21 @@ gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj
     }
     *out = qq.release();
     return GJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out) {
+    return query_create(ctx, rel_ids, n_rel, std::set<int32_t>(), out);
+}
+
+gj_status gj_query_create_projected(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
+                                    const int32_t *drop_attrs, int32_t n_drop, gj_query **out) {
+    if (n_drop < 0 || (n_drop > 0 && !drop_attrs)) return GJ_ERR_INVALID;
+    std::set<int32_t> drop(drop_attrs, drop_attrs + n_drop);
+    return query_create(ctx, rel_ids, n_rel, drop, out);
 }
 
 void gj_query_destroy(gj_query *q) {

@@ -211,17 +211,21 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             if (o.unit) o.unit[slot] = unit;
         }
         if (o.tile_first) {
-            // block `slot` holds rows [A, next block's A) of the result: the
-            // emit tiles whose first row lies there point at it
+            // the tile's blocks hold rows [s_A[0], s_end) of the result: every
+            // emit tile whose first row lies there points at the block holding
+            // that row (threads take tiles, not blocks, so one huge block
+            // costs no single thread more than its share)
             __syncthreads();
             const int64_t T = o.tile_rows;
-            for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
-                const uint64_t A = s_A[slot - o0];
-                const uint64_t end = slot + 1 < o1 ? s_A[slot + 1 - o0] : s_end;
-                const uint64_t lo = A > o.row0 ? A - o.row0 : 0;
-                const uint64_t hi = min(end - o.row0, (uint64_t)o.n);
-                for (int64_t t = (int64_t)((lo + T - 1) / T); t < o.tiles && (uint64_t)(t * T) < hi; t++)
-                    o.tile_first[t] = (uint32_t)slot;
+            const int ns = (int)(o1 - o0);
+            const uint64_t lo = s_A[0] > o.row0 ? s_A[0] - o.row0 : 0;
+            const uint64_t hi = min(s_end - o.row0, (uint64_t)o.n);
+            for (int64_t t = (int64_t)((lo + T - 1) / T) + threadIdx.x; t < o.tiles && (uint64_t)(t * T) < hi;
+                 t += DT) {
+                const uint64_t row = o.row0 + (uint64_t)(t * T);
+                int a = 0, b = ns;   // last block with first row <= row
+                while (a < b) { int m = (a + b) >> 1; if (s_A[m] <= row) a = m + 1; else b = m; }
+                o.tile_first[t] = (uint32_t)(o0 + a - 1);
             }
         }
     }

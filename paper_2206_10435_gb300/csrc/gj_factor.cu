@@ -120,11 +120,20 @@ __global__ void k_gather_cols(ColSet cs, const uint32_t *__restrict__ perm, int6
     }
 }
 
-__global__ void k_heads_sorted(const int32_t *__restrict__ sorted, int nk, int64_t n, uint8_t *head) {
+// the columns a factor groups by (its order; all key columns unless some
+// were projected away)
+struct ColIdx {
+    int n;
+    int idx[MAX_KEYS];
+};
+
+__global__ void k_heads_sorted(const int32_t *__restrict__ sorted, ColIdx by, int64_t n, uint8_t *head) {
     for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
         uint8_t h = (i == 0);
-        for (int c = 0; c < nk && !h; c++)
-            h = sorted[(int64_t)c * n + i] != sorted[(int64_t)c * n + i - 1];
+        for (int k = 0; k < by.n && !h; k++) {
+            const int64_t c = by.idx[k];
+            h = sorted[c * n + i] != sorted[c * n + i - 1];
+        }
         head[i] = h;
     }
 }
@@ -267,7 +276,10 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
         // once, then find heads and groups with sequential reads
         GJ_CUDA_TRY(dalloc(c, &sorted, (size_t)R.nk * n));
         k_gather_cols<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, sorted); c.launches++;
-        k_heads_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, R.nk, n, head); c.launches++;
+        ColIdx by{};
+        by.n = (int)order.size();
+        for (int i = 0; i < by.n; i++) by.idx[i] = order[i];
+        k_heads_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, by, n, head); c.launches++;
     }
     GJ_CUDA_TRY(cudaGetLastError());
     GJ_CUDA_TRY(scan_u32(c, nullptr, head, gid, n, gcount));

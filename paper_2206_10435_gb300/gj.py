@@ -103,6 +103,9 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_int64), _P, _P, _P]),
         "gj_query_create": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
                                            ctypes.POINTER(_P)]),
+        "gj_query_create_projected": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                     ctypes.POINTER(_P)]),
         "gj_query_destroy": (None, [_P]),
         "gj_query_sizes": (ctypes.c_int, [_P, ctypes.POINTER(QuerySizes)]),
         "gj_query_set_stream": (ctypes.c_int, [_P, _P]),
@@ -251,15 +254,23 @@ class Context:
                                       _P(_ptr(gstart)), _P(_ptr(gkey))), "gj_factor_export")
         return perm[:n_rows], gstart, gkey[:n_keys * G.value].view(n_keys, G.value)
 
-    def query(self, rel_ids) -> "Query":
-        return Query(self, rel_ids)
+    def query(self, rel_ids, drop_attrs=()) -> "Query":
+        """A query over the loaded relations rel_ids (root first); attributes
+        in drop_attrs are projected away early (gj_query_create_projected)."""
+        return Query(self, rel_ids, drop_attrs=drop_attrs)
 
 
 class Query:
-    def __init__(self, ctx: Context, rel_ids=None, handle=None):
+    def __init__(self, ctx: Context, rel_ids=None, handle=None, drop_attrs=()):
         self.ctx = ctx
         if handle is not None:
             h = handle
+        elif drop_attrs:
+            ids = _i32(list(rel_ids))
+            drop = _i32(list(drop_attrs))
+            h = _P()
+            _check(lib().gj_query_create_projected(ctx.h, ids, len(rel_ids), drop, len(drop_attrs),
+                                                   ctypes.byref(h)), "gj_query_create_projected")
         else:
             ids = _i32(list(rel_ids))
             h = _P()

@@ -11,13 +11,13 @@ def to_u64(t):
 
 
 class Run:
-    def __init__(self, ctx, query):
+    def __init__(self, ctx, query, drop=()):
         from paper_2206_10435_gb300 import gj
         self.ctx = ctx
         self.query = query
         self.ids = gj.load_query(ctx, query)
-        self.q = ctx.query(self.ids)
-        self.plan = O.plan(query)
+        self.q = ctx.query(self.ids, drop_attrs=drop)
+        self.plan = O.plan(query, drop)
 
     def summarize(self):
         return self.q.summarize()

@@ -176,6 +176,53 @@ def test_oracle_matches_nested_loops(q):
         assert int(gm_c[jj][1].sum()) == c.total   # each relation sums to |Q|
 
 
+def droppable(q):
+    """Attributes held by exactly one relation, keeping at least one key
+    column on the root (the attributes early projection may delete)."""
+    rels = q.relations
+    one = [a for R in rels for a in R.attrs if sum(S.attrs.count(a) for S in rels) == 1]
+    if rels and all(a in one for a in rels[0].attrs):
+        one = [a for a in one if a != rels[0].attrs[0]]
+    return sorted(set(one))
+
+
+@pytest.mark.parametrize("q", [q for q in tiny_queries() if droppable(q)][:80],
+                         ids=lambda q: q.name)
+def test_early_projection_matches_nested_loops(q):
+    """Section 3.7: deleting attributes held by one relation keeps the bag of
+    row-id tuples; rows are ordered by the remaining variables, then row ids;
+    levels are the per-prefix runs over the remaining variables."""
+    cand = droppable(q)
+    for drop in (cand[:1], cand):
+        full = O.plan(q)
+        pl = O.plan(q, drop)
+        assert pl.V == [a for a in full.V if a not in drop]
+        bf = canonical(q, brute_force(q), pl.V)
+        if not bf:
+            continue
+        j = O.join(q, drop=drop)
+        assert [tuple(t) for t in j.rowids.tolist()] == [tuple(t) for t in bf]
+        jf = O.join(q)
+        assert sorted(map(tuple, jf.rowids.tolist())) == sorted(map(tuple, j.rowids.tolist()))
+        cols = O.columns(q, j.rowids, drop)
+        assert len(cols) == len(pl.V) + sum(len(R.payloads) for R in q.relations)
+        for i, t in enumerate(bf[:50]):
+            assert [int(cols[v][i]) for v in range(len(pl.V))] == [value_of(q, t, a) for a in pl.V]
+        lv = O.gfjs_levels(q, j.rowids, drop)
+        ref = levels_by_definition(q, bf, pl.V)
+        for l in range(len(pl.V)):
+            assert [list(x) for x in zip(lv[l].value.tolist(), lv[l].freq.tolist(),
+                                         lv[l].offset.tolist())] == ref[l]
+
+
+def test_early_projection_rejects_shared_attributes():
+    q, _, _, _ = golden_fig.load()
+    with pytest.raises(ValueError):
+        O.plan(q, drop=[q.relations[0].attrs[1]])   # B joins R1 and R2
+    pl = O.plan(q, drop=[q.relations[0].attrs[0], q.relations[-1].attrs[-1]])
+    assert len(pl.V) == len(O.plan(q).V) - 2
+
+
 def test_cyclic_query_is_rejected():
     a = np.array([0, 1], np.int32)
     q = G.Query("triangle", [G.Relation("R", [0, 1], [a, a]),
