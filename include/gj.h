@@ -175,6 +175,15 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
  * Rows of the result are ordered by V (signed int32, ascending), ties broken
  * by the original row ids r_1..r_k (Def. 1 sorts the result by all columns).
  * Builds any factor it needs.
+ *
+ * One cyclic shape is accepted as well: three relations of two key columns
+ * each, every pair sharing exactly one attribute (R0(A,B), R1(B,C), R2(C,A)
+ * in any column order).  Its junction tree (Section 2.3) has the single
+ * cluster {A,B,C}, whose potential (Algorithm 1, the join of the three
+ * factors) is the summary: the triples of groups that close the cycle.  V
+ * is R0's columns in declared order, then C; rows are ordered as above.
+ * gj_summarize and gj_desummarize work as for a tree; gj_level,
+ * gj_summary_groups and gj_summary_save return GJ_ERR_INVALID for it.
  */
 gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out);
 

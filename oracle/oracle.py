@@ -27,6 +27,11 @@ Readings of the paper that this oracle fixes:
   do not exist (Section 3.3: entries below 1 are dropped).
 * Counts are exact below 2^64 - 1; that value marks a clamped count, and a
   join whose size reaches it is reported as overflowing.
+* The cyclic 3-way join R0(A,B), R1(B,C), R2(C,A) (any column order): V is
+  R0's columns in declared order, then C; the result (the same plain
+  definition: every row combination agreeing on all shared attributes) is
+  computed by sort-based equi-joins R0 |><| R1 on B, then with R2 on (C, A),
+  and put in canonical order by a sort.
 * Early projection (Section 3.7): a dropped attribute is deleted from V.
   The result is the same bag of row-id tuples, its columns are the
   remaining V attributes and the payloads, and its rows are ordered by the
@@ -102,10 +107,30 @@ class Plan:
     V: list            # attribute ids in summary-column order
     var_rel: list      # relation that introduces V[i]
     var_col: list      # its column there
+    cyclic: bool = False   # the 3-cycle R0(A,B), R1(B,C), R2(C,A)
+
+
+def _triangle(rels):
+    """(ab, bc, ca) if the relations form the cycle R0(A,B), R1(B,C), R2(C,A)."""
+    if len(rels) != 3 or any(len(R.attrs) != 2 or R.attrs[0] == R.attrs[1] for R in rels):
+        return None
+
+    def shared(x, y):
+        s = [a for a in rels[x].attrs if a in rels[y].attrs]
+        return s[0] if len(s) == 1 else None
+    ab, bc, ca = shared(0, 1), shared(1, 2), shared(2, 0)
+    if None in (ab, bc, ca) or len({ab, bc, ca}) != 3:
+        return None
+    return ab, bc, ca
 
 
 def plan(query, drop=()) -> Plan:
     rels = query.relations
+    tri = None if drop else _triangle(rels)
+    if tri:
+        ab, bc, ca = tri
+        return Plan([-1, 0, 1], [[], [ab], [bc, ca]], [0, 1, 2], list(rels[0].attrs) + [bc],
+                    [0, 0, 1], [0, 1, rels[1].attrs.index(bc)], cyclic=True)
     drop = set(drop)
     for a in drop:
         if sum(R.attrs.count(a) for R in rels) != 1:
@@ -187,10 +212,44 @@ class Counts:
     mult: list = None          # per relation, result tuples each row is in
 
 
+def _equi_join(left_keys, right_keys):
+    """All (i, j) with left_keys[i] == right_keys[j], i ascending, j
+    ascending within i (a sort of the right side, then ranges)."""
+    order = np.argsort(right_keys, kind="stable")
+    rs = right_keys[order]
+    lo = np.searchsorted(rs, left_keys, "left")
+    hi = np.searchsorted(rs, left_keys, "right")
+    cnt = (hi - lo).astype(np.int64)
+    li = np.repeat(np.arange(left_keys.shape[0], dtype=np.int64), cnt)
+    first = np.repeat(lo - (np.cumsum(cnt) - cnt), cnt)
+    return li, order[first + np.arange(li.shape[0], dtype=np.int64)]
+
+
+def _triangle_rowids(query, pl) -> np.ndarray:
+    """Row-id triples of the cyclic join, in canonical order."""
+    R0, R1, R2 = query.relations
+    ab, (bc, ca) = pl.sep[1][0], pl.sep[2]
+    col = lambda R, a: np.asarray(R.keys[R.attrs.index(a)], dtype=np.int64)
+    i0, i1 = _equi_join(col(R0, ab), col(R1, ab))
+    pair_ca = (col(R1, bc)[i1] << 32) | (col(R0, ca)[i0] & 0xFFFFFFFF)
+    r2_ca = (col(R2, bc) << 32) | (col(R2, ca) & 0xFFFFFFFF)
+    p, i2 = _equi_join(pair_ca, r2_ca)
+    t = np.stack([i0[p], i1[p], i2], axis=1).astype(np.int64)
+    v0 = np.asarray(R0.keys[0])[t[:, 0]]
+    v1 = np.asarray(R0.keys[1])[t[:, 0]]
+    vc = col(R1, bc)[t[:, 1]]
+    order = np.lexsort((t[:, 2], t[:, 1], t[:, 0], vc, v1, v0))
+    return t[order].astype(np.int32)
+
+
 def count(query, rows: bool = False) -> Counts:
     """Join size by the row-level counting pass (and per-row multiplicities)."""
-    lib = _load()
     pl = plan(query)
+    if pl.cyclic:
+        if rows:
+            raise NotImplementedError("per-row multiplicities of the cyclic join")
+        return Counts(int(_triangle_rowids(query, pl).shape[0]), False)
+    lib = _load()
     m = _Marshal(query, pl)
     k = len(query.relations)
     up = [np.zeros(max(R.n_rows, 1), dtype=np.uint64) for R in query.relations]
@@ -220,8 +279,13 @@ class Joined:
 def join(query, max_tuples: int = 50_000_000, drop=()) -> Joined:
     """Materialise the join (cascade of hash joins + canonical sort, by the
     V of the projection when attributes are dropped)."""
-    lib = _load()
     pl = plan(query, drop)
+    if pl.cyclic:
+        t = _triangle_rowids(query, pl)
+        if t.shape[0] > max_tuples:
+            raise ValueError(f"join result too large to materialise ({t.shape[0]} tuples)")
+        return Joined(t, [])
+    lib = _load()
     m = _Marshal(query, pl)
     k = len(query.relations)
     c = count(query)

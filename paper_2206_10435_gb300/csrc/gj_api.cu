@@ -345,6 +345,58 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
 
 namespace {
 
+// The cyclic 3-way join (gj_cycle.cu): three relations of two distinct key
+// attributes each, every pair sharing exactly one, the three shared
+// attributes distinct (R0(A,B), R1(B,C), R2(C,A) up to column order).  Fills
+// the plan: V = R0's columns in declared order, then R1's attribute C;
+// factor orders R0 declared, R1 (B, C), R2 (C, A); payloads as usual.
+bool plan_triangle(CtxState &cs, const int32_t *rel_ids, QueryState &q) {
+    Relation *R[3];
+    for (int j = 0; j < 3; j++) {
+        auto it = cs.rels.find(rel_ids[j]);
+        if (it == cs.rels.end()) return false;
+        R[j] = it->second.get();
+        if (R[j]->nk != 2 || R[j]->attr[0] == R[j]->attr[1]) return false;
+    }
+    // the attribute relations x and y share, if exactly one
+    auto shared = [&](int x, int y, int32_t &a) {
+        int n = 0;
+        for (int32_t v : R[x]->attr)
+            if (std::find(R[y]->attr.begin(), R[y]->attr.end(), v) != R[y]->attr.end()) { a = v; n++; }
+        return n == 1;
+    };
+    int32_t ab = 0, bc = 0, ca = 0;
+    if (!shared(0, 1, ab) || !shared(1, 2, bc) || !shared(2, 0, ca)) return false;
+    if (ab == bc || bc == ca || ca == ab) return false;
+    auto col = [&](int j, int32_t a) {
+        return (int)(std::find(R[j]->attr.begin(), R[j]->attr.end(), a) - R[j]->attr.begin());
+    };
+    q.tri = true;
+    // per relation: {shared with the previous one, shared with the next one}
+    q.tri_col[0][0] = col(0, ca); q.tri_col[0][1] = col(0, ab);
+    q.tri_col[1][0] = col(1, ab); q.tri_col[1][1] = col(1, bc);
+    q.tri_col[2][0] = col(2, bc); q.tri_col[2][1] = col(2, ca);
+    for (int j = 0; j < 3; j++) {
+        q.r[j].rel_id = rel_ids[j];
+        q.r[j].R = R[j];
+    }
+    q.r[0].new_cols = {0, 1};
+    q.r[1].parent = 0;
+    q.r[1].sep_cols = {col(1, ab)};
+    q.r[1].sep_cols_parent = {col(0, ab)};
+    q.r[1].new_cols = {col(1, bc)};
+    q.r[2].parent = 1;
+    q.r[2].sep_cols = {col(2, bc), col(2, ca)};
+    q.r[2].sep_cols_parent = {col(1, bc)};
+    q.pre = {0, 1, 2};
+    q.pos = {0, 1, 2};
+    for (int t = 0; t < 3; t++)
+        for (int c : q.r[t].new_cols) { q.var_rel.push_back(t); q.var_col.push_back(c); }
+    for (int j = 0; j < 3; j++)
+        for (int p = 0; p < R[j]->np; p++) { q.col_rel.push_back(j); q.col_pay.push_back(p); }
+    return true;
+}
+
 // Plans a query over the relations rel_ids (the first is the root) and gets
 // every relation's factor.  Attributes in `drop` are left out of the result
 // (early projection, Section 3.7): each must occur in exactly one relation,
@@ -372,6 +424,19 @@ gj_status query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
     q.cs = &ctx->s;
     q.k = n_rel;
     q.r.resize(n_rel);
+    if (n_rel == 3 && drop.empty() && plan_triangle(ctx->s, rel_ids, q)) {
+        DeviceGuard g(ctx->s.c.device);
+        for (int j = 0; j < 3; j++) {
+            QRel &t = q.r[j];
+            std::vector<int> order(t.sep_cols);
+            order.insert(order.end(), t.new_cols.begin(), t.new_cols.end());
+            gj_status st = GJ_OK;
+            t.F = get_factor(ctx->s, *t.R, order, &st);
+            if (!t.F) return st;
+        }
+        *out = qq.release();
+        return GJ_OK;
+    }
     std::set<int32_t> seen;
     for (int j = 0; j < n_rel; j++) {
         auto it = ctx->s.rels.find(rel_ids[j]);
@@ -531,7 +596,7 @@ gj_status gj_summarize(gj_query *q, uint64_t *total) {
 
 gj_status gj_summary_groups(gj_query *q, int32_t rel, uint64_t *w_dev, uint64_t *mult_dev,
                             uint64_t *off_dev) {
-    if (!q || rel < 0 || rel >= q->s.k) return GJ_ERR_INVALID;
+    if (!q || rel < 0 || rel >= q->s.k || q->s.tri) return GJ_ERR_INVALID;
     if (!q->s.summarized && !q->s.overflow) return GJ_ERR_STATE;
     DeviceGuard g(q->s.cs->c.device);
     QRel &t = q->s.r[rel];

@@ -555,8 +555,54 @@ __global__ void k_level_write(LevelSpec s, const uint32_t *F_dev, const uint8_t 
 
 }  // namespace
 
+// The emit kernel's description of a query's output: for every relation
+// (query position j) its factor, its block groups grp[j] and its output
+// columns (key columns of V, then payloads).  False if the layout exceeds
+// the kernel's limits.
+bool make_emit_spec(QueryState &q, void *const *out_cols, uint32_t *const *rowid_cols,
+                    const uint32_t *const *grp, const uint64_t *A, Emit4Spec &s) {
+    s = Emit4Spec{};
+    if (q.k > EMIT_MAXR || (int)q.var_rel.size() > EMIT_MAXV || (int)q.col_rel.size() > EMIT_MAXP)
+        return false;
+    int nc = 0;
+    bool vec = true;
+    const int nv = (int)q.var_rel.size();
+    for (int j = 0; j < q.k; j++) {
+        s.gstart[j] = q.r[j].F->gstart;
+        s.perm[j] = q.r[j].F->perm;
+        s.rid_out[j] = rowid_cols ? rowid_cols[j] : nullptr;
+        s.grp[j] = grp[j];
+        s.col_off[j] = nc;
+        for (int v = 0; v < nv; v++) {
+            if (q.var_rel[v] != j) continue;
+            s.src[nc] = q.r[j].F->gkey + (int64_t)q.var_col[v] * q.r[j].F->G;
+            s.dst[nc] = out_cols[v];
+            s.kind[nc] = 0;
+            nc++;
+        }
+        for (size_t p = 0; p < q.col_rel.size(); p++) {
+            if (q.col_rel[p] != j) continue;
+            s.src[nc] = q.r[j].F->pay[q.col_pay[p]];
+            s.dst[nc] = out_cols[nv + p];
+            s.kind[nc] = q.r[j].R->pw[q.col_pay[p]] == 8 ? 2 : 1;
+            nc++;
+        }
+    }
+    s.col_off[q.k] = nc;
+    // 32-byte vector stores need 32-byte aligned columns
+    for (int i = 0; i < nc; i++) vec &= ((uintptr_t)s.dst[i] & 31) == 0;
+    s.vec = vec;
+    s.A = A;
+    s.err = q.ctx().err;
+    return true;
+}
+
+gj_status tri_desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
+                          uint32_t *const *rowid_cols, uint64_t *n_out);
+
 gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
                       uint32_t *const *rowid_cols, uint64_t *n_out) {
+    if (q.tri) return tri_desummarize(q, row0, nrows, out_cols, rowid_cols, n_out);
     Ctx &c = q.ctx();
     *n_out = 0;
     if (!q.summarized) return GJ_ERR_STATE;
@@ -585,36 +631,9 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
     if (q.k > 8 && c.prof) cudaEventRecord(c.event(), c.stream);
     if (q.k <= 8) {
         Emit4Spec s{};
-        int nc = 0;
-        bool vec = true;
-        const int nv = (int)q.var_rel.size();
-        for (int j = 0; j < q.k; j++) {
-            s.gstart[j] = q.r[j].F->gstart;
-            s.perm[j] = q.r[j].F->perm;
-            s.rid_out[j] = rowid_cols ? rowid_cols[j] : nullptr;
-            s.grp[j] = f.grp[q.pos[j]];
-            s.col_off[j] = nc;
-            for (int v = 0; v < nv; v++) {
-                if (q.var_rel[v] != j) continue;
-                s.src[nc] = q.r[j].F->gkey + (int64_t)q.var_col[v] * q.r[j].F->G;
-                s.dst[nc] = out_cols[v];
-                s.kind[nc] = 0;
-                nc++;
-            }
-            for (size_t p = 0; p < q.col_rel.size(); p++) {
-                if (q.col_rel[p] != j) continue;
-                s.src[nc] = q.r[j].F->pay[q.col_pay[p]];
-                s.dst[nc] = out_cols[nv + p];
-                s.kind[nc] = q.r[j].R->pw[q.col_pay[p]] == 8 ? 2 : 1;
-                nc++;
-            }
-        }
-        s.col_off[q.k] = nc;
-        // 32-byte vector stores need 32-byte aligned columns
-        for (int i = 0; i < nc; i++) vec &= ((uintptr_t)s.dst[i] & 31) == 0;
-        s.vec = vec;
-        s.A = f.A;
-        s.err = c.err;
+        std::vector<const uint32_t *> grp(q.k);
+        for (int j = 0; j < q.k; j++) grp[j] = f.grp[q.pos[j]];
+        make_emit_spec(q, out_cols, rowid_cols, grp.data(), f.A, s);
         e = launch_emit(c, q.k, s, f.F_dev, row0, (int64_t)n, tm.tile_first);
     } else {
         EmitSpec s{};
@@ -665,6 +684,7 @@ gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, in
                      uint64_t *freq, uint64_t *off, uint64_t cap, uint64_t *n_out) {
     Ctx &c = q.ctx();
     *n_out = 0;
+    if (q.tri) return GJ_ERR_INVALID;   // the cyclic join's summary is its block list
     if (!q.summarized) return GJ_ERR_STATE;
     if (q.overflow) return GJ_ERR_OVERFLOW;
     if (level < 0 || level >= (int)q.var_rel.size()) return GJ_ERR_INVALID;

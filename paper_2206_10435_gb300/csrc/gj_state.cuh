@@ -111,6 +111,15 @@ struct QueryState {
     bool summarized = false;
     bool overflow = false;
     uint64_t total = 0;
+    // the cyclic 3-way join (gj_cycle.cu): key columns per relation
+    // {shared with the previous relation, shared with the next} in the
+    // cycle R0 -> R1 -> R2 -> R0, and its blocks (group triples) in result
+    // order with their first rows
+    bool tri = false;
+    int tri_col[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    uint64_t nblocks = 0;
+    uint64_t *blk_A = nullptr;
+    uint32_t *blk_grp[3] = {nullptr, nullptr, nullptr};
     // relations (with their factors) owned by a summary loaded from a file
     std::vector<std::unique_ptr<Relation>> loaded;
 };

@@ -259,7 +259,11 @@ cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
 
 }  // namespace
 
+void tri_free(Ctx &c, QueryState &q);
+gj_status tri_summarize(QueryState &q, uint64_t *total_out);
+
 void query_free_summary(Ctx &c, QueryState &q) {
+    tri_free(c, q);
     for (auto &t : q.r) {
         dfree(c, t.S_dev);
         dfree(c, t.L_dev);
@@ -281,6 +285,7 @@ void query_free_summary(Ctx &c, QueryState &q) {
 }
 
 gj_status summarize(QueryState &q, uint64_t *total_out) {
+    if (q.tri) return tri_summarize(q, total_out);
     Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;

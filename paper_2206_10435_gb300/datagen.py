@@ -142,6 +142,20 @@ def chain5_zipf(seed: int = SEED_BASE + 1, rows: int = 10**7, domain: int = 10**
                        np.int64, seed, aligned)
 
 
+def triangle_query(seed: int, rows, domain: int, s: float = 0.0, payload_dtype=np.int64,
+                   name: str = "triangle") -> Query:
+    """The cyclic join R(A,B) join S(B,C) join T(C,A): rows[i] rows per table,
+    keys Zipf(s) over [0, domain) (uniform for s = 0), one payload per table."""
+    rng = np.random.default_rng(seed)
+    rels = []
+    for i, (x, y) in enumerate([(0, 1), (1, 2), (2, 0)]):
+        n = int(rows[i])
+        cols = [zipf_keys(rng, n, s, domain), zipf_keys(rng, n, s, domain)]
+        pays = [_payload(rng, n, payload_dtype)] if payload_dtype is not None else []
+        rels.append(Relation("RST"[i], [x, y], cols, pays))
+    return Query(name, rels, {0: "A", 1: "B", 2: "C"})
+
+
 def star_poisson(seed: int = SEED_BASE + 2, fact_rows: int = 10**8, domain: int = 10**6,
                  n_dims: int = 4, lam: float = 2.0) -> Query:
     """Fact F(K_1..K_n, P) with K_j uniform over [0, domain), joined to

@@ -172,19 +172,21 @@ def test_dead_branch_does_not_overflow(ctx):
 
 
 def test_rejects_cyclic_and_disconnected(ctx):
+    # a 4-cycle is neither a join tree nor the supported 3-cycle
     from paper_2206_10435_gb300 import gj
     a = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
     r = ctx.load_relation([a, a], [0, 1])
     s = ctx.load_relation([a, a], [1, 2])
-    t = ctx.load_relation([a, a], [2, 0])
+    t = ctx.load_relation([a, a], [2, 3])
+    v = ctx.load_relation([a, a], [3, 0])
     u = ctx.load_relation([a], [9])
     with pytest.raises(gj.GJError) as e:
-        ctx.query([r, s, t])
+        ctx.query([r, s, t, v])
     assert e.value.status == gj.GJ_ERR_NOT_ACYCLIC
     with pytest.raises(gj.GJError) as e:
         ctx.query([r, u])
     assert e.value.status == gj.GJ_ERR_INVALID
-    for x in (r, s, t, u):
+    for x in (r, s, t, v, u):
         ctx.release_relation(x)
 
 

@@ -223,13 +223,55 @@ def test_early_projection_rejects_shared_attributes():
     assert len(pl.V) == len(O.plan(q).V) - 2
 
 
-def test_cyclic_query_is_rejected():
+def tiny_triangles():
+    qs = []
+    for seed in range(60):
+        q = G.triangle_query(7000 + seed, [1 + seed % 5, 1 + (seed // 5) % 4, 1 + (seed // 3) % 5],
+                             domain=2 + seed % 3, payload_dtype=np.int32 if seed % 2 else np.int64)
+        if seed % 4 in (1, 3):   # columns in another declared order
+            r = 2 if seed % 4 == 1 else 0
+            R = q.relations[r]
+            q.relations[r] = G.Relation(R.name, R.attrs[::-1], R.keys[::-1], R.payloads)
+        qs.append(q)
+    return qs
+
+
+@pytest.mark.parametrize("q", tiny_triangles(), ids=lambda q: f"tri{id(q) % 997}")
+def test_cyclic_triangle_matches_nested_loops(q):
+    """The 3-cycle's result: every row combination agreeing on A, B and C,
+    ordered by R0's columns, then C, then the row ids."""
+    pl = O.plan(q)
+    assert pl.cyclic and pl.V == list(q.relations[0].attrs) + [2]   # V = R0's columns, then C
+    bf = canonical(q, brute_force(q), pl.V)
+    assert O.count(q).total == len(bf)
+    j = O.join(q)
+    assert [tuple(t) for t in j.rowids.tolist()] == [tuple(t) for t in bf]
+    cols = O.columns(q, j.rowids)
+    for i, t in enumerate(bf[:50]):
+        assert [int(cols[v][i]) for v in range(3)] == [value_of(q, t, a) for a in pl.V]
+    lv = O.gfjs_levels(q, j.rowids)
+    ref = levels_by_definition(q, bf, pl.V)
+    for l in range(3):
+        assert [list(x) for x in zip(lv[l].value.tolist(), lv[l].freq.tolist(),
+                                     lv[l].offset.tolist())] == ref[l]
+
+
+def test_cyclic_triangle_all_equal_keys_gives_product():
+    q = G.triangle_query(1, [7, 5, 3], domain=1)
+    assert O.count(q).total == 7 * 5 * 3
+
+
+def test_other_cyclic_queries_are_rejected():
+    # a 4-cycle, and a triangle one of whose relations holds a third key:
+    # neither is a join tree nor the supported 3-cycle
     a = np.array([0, 1], np.int32)
-    q = G.Query("triangle", [G.Relation("R", [0, 1], [a, a]),
-                             G.Relation("S", [1, 2], [a, a]),
-                             G.Relation("T", [2, 0], [a, a])])
-    with pytest.raises(O.NotAcyclic):
-        O.plan(q)
+    q4 = G.Query("square", [G.Relation("R", [0, 1], [a, a]), G.Relation("S", [1, 2], [a, a]),
+                            G.Relation("T", [2, 3], [a, a]), G.Relation("U", [3, 0], [a, a])])
+    q3 = G.Query("triangle3", [G.Relation("R", [0, 1, 4], [a, a, a]), G.Relation("S", [1, 2], [a, a]),
+                               G.Relation("T", [2, 0], [a, a])])
+    for q in (q4, q3):
+        with pytest.raises(O.NotAcyclic):
+            O.plan(q)
 
 
 def test_plan_of_branching_tree():
