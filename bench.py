@@ -38,8 +38,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gj", choices=["gj", "reference"])
     p.add_argument("--workload", default="chain5_zipf",
-                   choices=["chain5_zipf", "chain3_uniform", "star_poisson", "batch", "serve",
-                            "reuse", "sensitivity"])
+                   choices=["chain5_zipf", "chain3_uniform", "star_poisson", "triangle", "batch",
+                            "serve", "reuse", "sensitivity"])
     p.add_argument("--rates", default="100,200,500,1000,2000,5000,10000",
                    help="serve workload: offered arrival rates (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -70,6 +70,10 @@ def workload_name(a):
         return ("chain3_uniform: R1(A,B) R2(B,C) R3(C,D), 10^4 rows/table, int32 keys, A,D "
                 "uniform over [0,10^4), B,C uniform over [0,1000), int32 payload/table, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks" + drop_note(a))
+    if a.workload == "triangle":
+        return ("triangle: cyclic R(A,B) S(B,C) T(C,A), 10^6 rows/table, int32 keys uniform over "
+                "[0,1000), int64 payload/table, one-cluster junction tree, "
+                f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "star_poisson":
         return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
                 "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "
@@ -94,6 +98,8 @@ def make_query(a, rank):
         return G.chain3_uniform(seed=G.SEED_BASE + 0 + 1000 * rank)
     if a.workload == "star_poisson":
         return G.star_poisson(seed=G.SEED_BASE + 2 + 1000 * rank)
+    if a.workload == "triangle":
+        return G.triangle_query(G.SEED_BASE + 5 + 1000 * rank, [10**6] * 3, domain=1000)
     return G.chain5_zipf(seed=G.SEED_BASE + 1 + 1000 * rank, rows=a.rows, domain=a.domain,
                          s=a.zipf)
 
@@ -252,7 +258,7 @@ def reduce_over_ranks(dist, elapsed_ms: float, rows: int, device):
     return float(t.item()), int(r.item())
 
 
-DEFAULT_SAMPLE = {"chain5_zipf": 20000, "chain3_uniform": 10**4, "star_poisson": 10**6,
+DEFAULT_SAMPLE = {"chain5_zipf": 20000, "chain3_uniform": 10**4, "star_poisson": 10**6, "triangle": 10000,
                   "batch": 0, "serve": 0, "reuse": 0, "sensitivity": 0}
 
 

@@ -349,7 +349,7 @@ namespace {
 // attributes each, every pair sharing exactly one, the three shared
 // attributes distinct (R0(A,B), R1(B,C), R2(C,A) up to column order).  Fills
 // the plan: V = R0's columns in declared order, then R1's attribute C;
-// factor orders R0 declared, R1 (B, C), R2 (C, A); payloads as usual.
+// factor orders R0 declared, R1 (B, C), R2 (A, C); payloads as usual.
 bool plan_triangle(CtxState &cs, const int32_t *rel_ids, QueryState &q) {
     Relation *R[3];
     for (int j = 0; j < 3; j++) {
@@ -386,7 +386,7 @@ bool plan_triangle(CtxState &cs, const int32_t *rel_ids, QueryState &q) {
     q.r[1].sep_cols_parent = {col(0, ab)};
     q.r[1].new_cols = {col(1, bc)};
     q.r[2].parent = 1;
-    q.r[2].sep_cols = {col(2, bc), col(2, ca)};
+    q.r[2].sep_cols = {col(2, ca), col(2, bc)};   // factor ordered by (A, C)
     q.r[2].sep_cols_parent = {col(1, bc)};
     q.pre = {0, 1, 2};
     q.pos = {0, 1, 2};

@@ -11,16 +11,19 @@
 // kernel expands (rows of a block ordered by r_R, r_S, r_T, the last
 // fastest), so the cyclic query reuses it unchanged.
 //
-// The cluster potential is built from the sorted factors, in result order:
-//   1. per R group (a, b) (R's factor order), the S groups with key b form
-//      one contiguous segment of S's factor, ordered by (b, c): its wedges;
-//   2. an exclusive scan numbers the wedges; one thread per wedge looks its
-//      closing edge (c, a) up in T's factor, ordered by (c, a);
-//   3. a scan over the hits numbers the blocks; each writes its three groups
-//      and its row count (saturating product); a saturating scan gives the
-//      blocks' first rows and |Q|.
-// Wedges are walked in R-group order and, inside, in c order, so blocks come
-// out ordered by (V_0, V_1, c) with V the root's columns then C.
+// The cluster potential is built from the sorted factors, in result order,
+// by sorted-list intersection (one warp per R group (a, b), R's factor
+// order):
+//   * S's factor is ordered by (b, c) and T's by (a, c), so the S groups with
+//     key b and the T groups with key a are two segments sorted by c;
+//   * the warp walks the shorter segment in c order and binary-searches the
+//     longer one: every c found in both closes the cycle;
+//   * a first pass counts each R group's triples, an exclusive scan places
+//     them, and a second pass writes every block's three groups and its row
+//     count (saturating product) in c order (ballots keep the lanes' order);
+//     a saturating scan gives the blocks' first rows and |Q|.
+// R groups come in R's order and each one's triples in c order, so blocks
+// are ordered by (V_0, V_1, c) with V the root's columns then C.
 #include <string.h>
 
 #include <algorithm>
@@ -44,15 +47,10 @@ struct TriSpec {
     const int32_t *b1, *c1;         // S's groups, ordered by (b, c)
     const uint32_t *gs1;
     int64_t G1;
-    const int32_t *c2, *a2;         // T's groups, ordered by (c, a)
+    const int32_t *c2, *a2;         // T's groups, ordered by (a, c)
     const uint32_t *gs2;
     int64_t G2;
 };
-
-inline int grid_for(Ctx &c, int64_t n) {
-    int64_t b = ceil_div(n, CT);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)c.num_sms * 16));
-}
 
 // first index in [lo, hi) whose key exceeds x (keys ascending)
 __device__ __forceinline__ uint32_t upper_i32(const int32_t *k, uint32_t lo, uint32_t hi, int32_t x) {
@@ -70,68 +68,88 @@ __device__ __forceinline__ uint32_t lower_i32(const int32_t *k, uint32_t lo, uin
     return lo;
 }
 
-// S's segment of every R group, and the exact number of wedges (64-bit)
-__global__ void k_tri_deg(TriSpec s, uint32_t *lo, uint32_t *deg, unsigned long long *wsum) {
+// the segments of R group i: S groups with key b, T groups with key a
+__device__ __forceinline__ void tri_segments(const TriSpec &s, int64_t i, uint32_t &sl, uint32_t &sh,
+                                             uint32_t &tl, uint32_t &th) {
+    const int32_t a = s.a0[i], b = s.b0[i];
+    sl = lower_i32(s.b1, 0, (uint32_t)s.G1, b);
+    sh = upper_i32(s.b1, sl, (uint32_t)s.G1, b);
+    tl = lower_i32(s.a2, 0, (uint32_t)s.G2, a);
+    th = upper_i32(s.a2, tl, (uint32_t)s.G2, a);
+}
+
+// One lane's element k of R group i's shorter segment and its partner in
+// the other one: true if both hold the same c.  *j gets the S group, *t the
+// T group.
+__device__ __forceinline__ bool tri_match(const TriSpec &s, bool walk_s, uint32_t k, uint32_t sl,
+                                          uint32_t sh, uint32_t tl, uint32_t th, uint32_t *j,
+                                          uint32_t *t) {
+    if (walk_s) {
+        const uint32_t jj = sl + k;
+        const int32_t c = s.c1[jj];
+        const uint32_t tt = lower_i32(s.c2, tl, th, c);
+        *j = jj;
+        *t = tt;
+        return tt < th && s.c2[tt] == c;
+    }
+    const uint32_t tt = tl + k;
+    const int32_t c = s.c2[tt];
+    const uint32_t jj = lower_i32(s.c1, sl, sh, c);
+    *j = jj;
+    *t = tt;
+    return jj < sh && s.c1[jj] == c;
+}
+
+constexpr int TRI_WARPS = CT / 32;
+
+// pass 1: triples per R group (a warp per group) and their exact total
+__global__ void k_tri_count(TriSpec s, uint32_t *cnt, unsigned long long *total) {
+    const int lane = threadIdx.x & 31;
     unsigned long long mine = 0;
-    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < s.G0; i += (int64_t)gridDim.x * CT) {
-        const int32_t b = s.b0[i];
-        const uint32_t l = lower_i32(s.b1, 0, (uint32_t)s.G1, b);
-        const uint32_t h = upper_i32(s.b1, l, (uint32_t)s.G1, b);
-        lo[i] = l;
-        deg[i] = h - l;
-        mine += h - l;
+    for (int64_t i = (int64_t)blockIdx.x * TRI_WARPS + (threadIdx.x >> 5); i < s.G0;
+         i += (int64_t)gridDim.x * TRI_WARPS) {
+        uint32_t sl, sh, tl, th;
+        tri_segments(s, i, sl, sh, tl, th);
+        const bool walk_s = sh - sl <= th - tl;
+        const uint32_t len = (sl == sh || tl == th) ? 0 : (walk_s ? sh - sl : th - tl);
+        uint32_t hits = 0;
+        for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+            uint32_t j, t;
+            const bool hit = k0 + lane < len && tri_match(s, walk_s, k0 + lane, sl, sh, tl, th, &j, &t);
+            hits += __popc(__ballot_sync(0xffffffffu, hit));
+        }
+        if (lane == 0) { cnt[i] = hits; mine += hits; }
     }
-    for (int d = 16; d; d >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, d);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(wsum, mine);
+    if (lane == 0 && mine) atomicAdd(total, mine);
 }
 
-// the T group holding (c, a), or NONE
-__device__ __forceinline__ uint32_t find_ca(const TriSpec &s, int32_t c, int32_t a) {
-    uint32_t l = lower_i32(s.c2, 0, (uint32_t)s.G2, c);
-    const uint32_t h = upper_i32(s.c2, l, (uint32_t)s.G2, c);
-    l = lower_i32(s.a2, l, h, a);
-    return (l < h && s.a2[l] == a) ? l : NONE;
-}
-
-// wedge w belongs to the last R group i with woff[i] <= w
-__device__ __forceinline__ uint32_t wedge_owner(const uint32_t *woff, int64_t G0, uint64_t w) {
-    uint32_t lo = 0, hi = (uint32_t)G0;
-    while (lo < hi) {
-        uint32_t m = lo + ((hi - lo) >> 1);
-        if ((uint64_t)woff[m] <= w) lo = m + 1; else hi = m;
-    }
-    return lo - 1;
-}
-
-__global__ void k_tri_check(TriSpec s, const uint32_t *__restrict__ lo, const uint32_t *__restrict__ woff,
-                            uint64_t nw, uint32_t *t_of, uint8_t *hit, uint32_t *err) {
-    for (uint64_t w = (uint64_t)blockIdx.x * CT + threadIdx.x; w < nw; w += (uint64_t)gridDim.x * CT) {
-        const uint32_t i = wedge_owner(woff, s.G0, w);
-        const uint32_t j = lo[i] + (uint32_t)(w - woff[i]);
-        uint32_t t = NONE;
-        if (i < s.G0 && j < s.G1) t = find_ca(s, s.c1[j], s.a0[i]);
-        else raise_err(err, ERRF_BOUNDS);
-        t_of[w] = t;
-        hit[w] = t != NONE;
-    }
-}
-
-__global__ void k_tri_write(TriSpec s, const uint32_t *__restrict__ lo, const uint32_t *__restrict__ woff,
-                            uint64_t nw, const uint32_t *__restrict__ t_of, const uint8_t *__restrict__ hit,
-                            const uint32_t *__restrict__ bidx, uint32_t *g0, uint32_t *g1, uint32_t *g2,
-                            uint64_t *W) {
-    for (uint64_t w = (uint64_t)blockIdx.x * CT + threadIdx.x; w < nw; w += (uint64_t)gridDim.x * CT) {
-        if (!hit[w]) continue;
-        const uint32_t i = wedge_owner(woff, s.G0, w);
-        const uint32_t j = lo[i] + (uint32_t)(w - woff[i]);
-        const uint32_t t = t_of[w];
-        const uint32_t b = bidx[w];
-        g0[b] = i;
-        g1[b] = j;
-        g2[b] = t;
-        const uint64_t c0 = s.gs0[i + 1] - s.gs0[i], c1 = s.gs1[j + 1] - s.gs1[j],
-                       c2 = s.gs2[t + 1] - s.gs2[t];
-        W[b] = sat_mul(sat_mul(c0, c1), c2);
+// pass 2: R group i's blocks at base[i] onwards, in c order
+__global__ void k_tri_blocks(TriSpec s, const uint32_t *__restrict__ base, uint32_t *g0, uint32_t *g1,
+                             uint32_t *g2, uint64_t *W) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    for (int64_t i = (int64_t)blockIdx.x * TRI_WARPS + (threadIdx.x >> 5); i < s.G0;
+         i += (int64_t)gridDim.x * TRI_WARPS) {
+        uint32_t sl, sh, tl, th;
+        tri_segments(s, i, sl, sh, tl, th);
+        const bool walk_s = sh - sl <= th - tl;
+        const uint32_t len = (sl == sh || tl == th) ? 0 : (walk_s ? sh - sl : th - tl);
+        uint32_t at = base[i];
+        const uint64_t c0 = s.gs0[i + 1] - s.gs0[i];
+        for (uint32_t k0 = 0; k0 < len; k0 += 32) {
+            uint32_t j = 0, t = 0;
+            const bool hit = k0 + lane < len && tri_match(s, walk_s, k0 + lane, sl, sh, tl, th, &j, &t);
+            const uint32_t m = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+                const uint32_t b = at + __popc(m & below);
+                g0[b] = (uint32_t)i;
+                g1[b] = j;
+                g2[b] = t;
+                const uint64_t c1 = s.gs1[j + 1] - s.gs1[j], c2 = s.gs2[t + 1] - s.gs2[t];
+                W[b] = sat_mul(sat_mul(c0, c1), c2);
+            }
+            at += __popc(m);
+        }
     }
 }
 
@@ -189,16 +207,15 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
     tri_free(c, q);
     q.summarized = false;
     const TriSpec s = tri_spec(q);
-    uint32_t *lo = nullptr, *deg = nullptr, *woff = nullptr, *cnt = nullptr, *t_of = nullptr,
-             *bidx = nullptr;
-    uint8_t *hit = nullptr;
+    uint32_t *hits = nullptr, *base = nullptr, *cnt = nullptr;
     uint64_t *W = nullptr, *total_dev = nullptr;
-    unsigned long long *wsum = nullptr;
-    unsigned long long nw_exact = 0;
-    uint32_t nw32 = 0, nb32 = 0;
+    unsigned long long *tsum = nullptr;
+    unsigned long long nb = 0;
     uint64_t total = 0;
     gj_status st = GJ_OK;
     cudaError_t e = cudaSuccess;
+    const int64_t warps_grid = std::max<int64_t>(
+        1, std::min<int64_t>(ceil_div(s.G0, TRI_WARPS), (int64_t)c.num_sms * 16));
 #define TRY(x)                                                 \
     do {                                                       \
         e = (x);                                               \
@@ -207,48 +224,34 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
             goto fail;                                         \
         }                                                      \
     } while (0)
-    TRY(dalloc(c, &cnt, 2));
+    TRY(dalloc(c, &cnt, 1));
     TRY(dalloc(c, &total_dev, 1));
+    TRY(dalloc(c, &tsum, 1));
+    TRY(cudaMemsetAsync(tsum, 0, sizeof(unsigned long long), c.stream));
     if (s.G0 > 0 && s.G1 > 0 && s.G2 > 0) {
-        // 1. wedges per R group
-        TRY(dalloc(c, &lo, s.G0));
-        TRY(dalloc(c, &deg, s.G0));
-        TRY(dalloc(c, &woff, s.G0));
-        TRY(dalloc(c, &wsum, 1));
-        TRY(cudaMemsetAsync(wsum, 0, sizeof(unsigned long long), c.stream));
-        k_tri_deg<<<grid_for(c, s.G0), CT, 0, c.stream>>>(s, lo, deg, wsum); c.launches++;
+        // triples per R group, placed by a scan
+        TRY(dalloc(c, &hits, s.G0));
+        TRY(dalloc(c, &base, s.G0));
+        k_tri_count<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, hits, tsum); c.launches++;
         TRY(cudaGetLastError());
-        TRY(readback(c, wsum, &nw_exact, 8));
-        // wedges are numbered in 32 bits
-        if (nw_exact > 0x7fffffffull) { st = GJ_ERR_CAPACITY; goto done; }
-        TRY(scan_u32(c, deg, nullptr, woff, s.G0, cnt));
-        TRY(readback(c, cnt, &nw32, 4));
-        uint64_t nw = nw32;
-        if (nw != nw_exact) { st = GJ_ERR_CUDA; goto done; }   // cannot happen
-        if (nw > 0) {
-            // 2. closing edges, 3. blocks
-            TRY(dalloc(c, &t_of, nw));
-            TRY(dalloc(c, &hit, nw));
-            TRY(dalloc(c, &bidx, nw));
-            k_tri_check<<<grid_for(c, (int64_t)nw), CT, 0, c.stream>>>(s, lo, woff, nw, t_of, hit, c.err); c.launches++;
+        TRY(readback(c, tsum, &nb, 8));
+        // blocks are numbered in 32 bits
+        if (nb > 0x7fffffffull) { st = GJ_ERR_CAPACITY; goto done; }
+        if (nb > 0) {
+            TRY(scan_u32(c, hits, nullptr, base, s.G0, cnt));
+            for (auto &g : q.blk_grp) TRY(dalloc(c, &g, nb));
+            TRY(dalloc(c, &W, nb));
+            TRY(dalloc(c, &q.blk_A, nb));
+            k_tri_blocks<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, base, q.blk_grp[0], q.blk_grp[1],
+                                                                    q.blk_grp[2], W); c.launches++;
             TRY(cudaGetLastError());
-            TRY(scan_u32(c, nullptr, hit, bidx, (int64_t)nw, cnt + 1));
-            TRY(readback(c, cnt + 1, &nb32, 4));
-            if (nb32 > 0) {
-                for (auto &g : q.blk_grp) TRY(dalloc(c, &g, nb32));
-                TRY(dalloc(c, &W, nb32));
-                TRY(dalloc(c, &q.blk_A, nb32));
-                k_tri_write<<<grid_for(c, (int64_t)nw), CT, 0, c.stream>>>(
-                    s, lo, woff, nw, t_of, hit, bidx, q.blk_grp[0], q.blk_grp[1], q.blk_grp[2], W); c.launches++;
-                TRY(cudaGetLastError());
-                TRY(scan_u64_sat(c, W, nullptr, q.blk_A, nb32, total_dev, nullptr, nullptr));
-                TRY(readback(c, total_dev, &total, 8));
-            }
+            TRY(scan_u64_sat(c, W, nullptr, q.blk_A, (int64_t)nb, total_dev, nullptr, nullptr));
+            TRY(readback(c, total_dev, &total, 8));
         }
     }
     st = check_device_error(c);
     if (st != GJ_OK) goto done;
-    q.nblocks = nb32;
+    q.nblocks = nb;
     q.total = total;
     q.overflow = total == SAT;
     q.summarized = true;
@@ -260,16 +263,12 @@ fail:
 done:
 #undef TRY
     if (!q.summarized) tri_free(c, q);
-    dfree(c, lo);
-    dfree(c, deg);
-    dfree(c, woff);
+    dfree(c, hits);
+    dfree(c, base);
     dfree(c, cnt);
-    dfree(c, t_of);
-    dfree(c, hit);
-    dfree(c, bidx);
     dfree(c, W);
     dfree(c, total_dev);
-    dfree(c, wsum);
+    dfree(c, tsum);
     return st;
 }
 
