@@ -178,9 +178,10 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
  *
  * One cyclic shape is accepted as well: three relations of two key columns
  * each, every pair sharing exactly one attribute (R0(A,B), R1(B,C), R2(C,A)
- * in any column order).  Its junction tree (Section 2.3) has the single
- * cluster {A,B,C}, whose potential (Algorithm 1, the join of the three
- * factors) is the summary: the triples of groups that close the cycle.  V
+ * in any column order).  Its junction tree has the single maxclique
+ * {A,B,C}, whose joint potential (Section 3.2.1, Algorithm 1: the join of
+ * the three factors, frequencies multiplied) is the summary: the triples of
+ * groups that close the cycle.  V
  * is R0's columns in declared order, then C; rows are ordered as above.
  * gj_summarize and gj_desummarize work as for a tree; gj_level,
  * gj_summary_groups and gj_summary_save return GJ_ERR_INVALID for it.

@@ -1,15 +1,16 @@
 // gj_cycle.cu -- the cyclic 3-way join R(A,B) |><| S(B,C) |><| T(C,A).
 //
-// A cycle has no join tree.  The paper builds a junction tree instead
-// (Section 2.3: min-fill-in triangulation of the moral graph) and computes
-// the potential of every cluster as the join of the potentials of its
-// relations (Algorithm 1).  For three relations pairwise sharing one
-// attribute the triangulation leaves one cluster {A, B, C}, so the summary
-// is that cluster's potential: every triple of groups (g_R, g_S, g_T) with
-// g_R = (a, b), g_S = (b, c), g_T = (c, a), holding cnt_R * cnt_S * cnt_T
-// result rows.  These triples are exactly the blocks the desummarise emit
-// kernel expands (rows of a block ordered by r_R, r_S, r_T, the last
-// fastest), so the cyclic query reuses it unchanged.
+// A cycle has no join tree.  The paper turns the query graph into a
+// junction tree whose maxcliques may hold potentials from several tables
+// and joins those into one potential per maxclique (Section 3.2.1,
+// Algorithm 1; inference on graphs, Section 3.4).  For three relations
+// pairwise sharing one attribute there is one maxclique {A, B, C}, and its
+// joint potential is the summary: every triple of groups (g_R, g_S, g_T)
+// with g_R = (a, b), g_S = (b, c), g_T = (c, a), with frequency
+// cnt_R * cnt_S * cnt_T (the paper's example: entries (a1,b1,5),
+// (b1,c1,10), (c1,a1,20) give (a1,b1,c1,1000)).  These triples are exactly
+// the blocks the desummarise emit kernel expands (rows of a block ordered by
+// r_R, r_S, r_T, the last fastest), so the cyclic query reuses it unchanged.
 //
 // The cluster potential is built from the sorted factors, in result order,
 // by sorted-list intersection (one warp per R group (a, b), R's factor

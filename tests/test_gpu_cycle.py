@@ -8,7 +8,7 @@ import pytest
 from oracle import oracle as O
 from paper_2206_10435_gb300 import datagen as G
 from tests.gpu_util import Run
-from tests.test_oracle import tiny_triangles
+from tests.test_oracle import _paper_triangle, tiny_triangles
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,6 +45,11 @@ def triangle_parity(ctx, q, windows=()):
                 assert np.array_equal(a, b[r0:r0 + m])
     run.close()
     return total
+
+
+def test_paper_example(ctx):
+    # Section 3.2.1: entries (a1,b1,5), (b1,c1,10), (c1,a1,20) -> (a1,b1,c1,1000)
+    assert triangle_parity(ctx, _paper_triangle(), windows=[(999, 5)]) == 1010
 
 
 @pytest.mark.parametrize("i", range(60))

@@ -256,6 +256,29 @@ def test_cyclic_triangle_matches_nested_loops(q):
                                      lv[l].offset.tolist())] == ref[l]
 
 
+def _paper_triangle():
+    """Section 3.2.1's example: T1(A,B), T2(B,C), T3(C,A) with the entries
+    (a1,b1) x5, (b1,c1) x10, (c1,a1) x20, plus rows that close no cycle."""
+    def rel(name, attrs, pairs):
+        x = np.array([p[0] for p in pairs], np.int32)
+        y = np.array([p[1] for p in pairs], np.int32)
+        return G.Relation(name, attrs, [x, y], [np.arange(len(pairs), dtype=np.int64)])
+    t1 = rel("T1", [0, 1], [(1, 1)] * 5 + [(2, 1), (1, 3)])
+    t2 = rel("T2", [1, 2], [(1, 1)] * 10 + [(3, 7)])
+    t3 = rel("T3", [2, 0], [(1, 1)] * 20 + [(1, 2), (7, 9)])
+    return G.Query("paper_triangle", [t1, t2, t3], {0: "A", 1: "B", 2: "C"})
+
+
+def test_cyclic_triangle_paper_example_gives_1000():
+    # the joint potential's entry (a1, b1, c1) has frequency 5 * 10 * 20; the
+    # added rows give one more entry (a2, b1, c1) of frequency 1 * 10 * 1, and
+    # (a1, b3, c7) does not close (T3 holds (c7, a9), not (c7, a1))
+    q = _paper_triangle()
+    assert O.count(q).total == 5 * 10 * 20 + 1 * 10 * 1
+    bf = canonical(q, brute_force(q), O.plan(q).V)
+    assert len(bf) == 1010
+
+
 def test_cyclic_triangle_all_equal_keys_gives_product():
     q = G.triangle_query(1, [7, 5, 3], domain=1)
     assert O.count(q).total == 7 * 5 * 3
