@@ -302,14 +302,16 @@ def main():
     CH = 1 << a.chunk_log2
     out_bufs = None
     phase = {"build_ms": 0.0, "summary_ms": 0.0, "desum_ms": 0.0}
+    groups = []
 
     def step(record=False):
-        nonlocal out_bufs
+        nonlocal out_bufs, groups
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
         if record:
             ev[0].record(stream)
         ids = [ctx.load_relation(ks, attrs, ps) for ks, ps, attrs in rels]
         qq = ctx.query(ids, drop_attrs=drop_list(a))   # factor construction
+        groups = list(qq.n_groups)
         if record:
             ev[1].record(stream)
         total = qq.summarize()                    # upward + downward passes
@@ -377,6 +379,31 @@ def main():
                 "avg_launch_ms": prof["emit_ms"] / max(prof["emit_launches"], 1),
                 "expand_ms_per_step": prof["expand_ms"] / a.steps,
                 "emit_ms_per_step": prof["emit_ms"] / a.steps}
+    # the other phases against the same roofline, with the algorithmic bytes
+    # of the hot-path definitions: factor build reads every key column and
+    # payload once, writes the row order, the payloads in group order and per
+    # group its keys and start; the summary reads per group its keys and
+    # count and writes w, mult and off (8 B each)
+    build_b = summ_b = 0
+    for (ks, ps, _), G in zip(rels, groups):
+        n = ks[0].numel() if ks else 0
+        k = len(ks)
+        w = sum(t.element_size() for t in ps)
+        build_b += n * (4 * k + 4 + 2 * w) + G * (4 * k + 4)
+        summ_b += G * (4 * k + 4 + 24)
+    phase_rooflines = {}
+    for name, b, ms in (("factor_build", build_b, phase["build_ms"]),
+                        ("summary", summ_b, phase["summary_ms"])):
+        if name == "summary" and a.workload == "triangle":
+            # the cyclic join's summary is its maxclique potential (an
+            # intersection of sorted segments), not a pass over groups
+            phase_rooflines[name] = {"algorithmic_bytes": None, "ms": ms, "achieved": None,
+                                     "unit": "GB/s", "frac": None,
+                                     "note": "maxclique potential: no per-group byte count"}
+            continue
+        gbs = b / (ms * 1e6) if ms else None
+        phase_rooflines[name] = {"algorithmic_bytes": b, "ms": ms, "achieved": gbs, "unit": "GB/s",
+                                 "frac": gbs / peak if gbs else None}
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(a, q, a.cpu_sample_rows, drop_list(a))
@@ -394,6 +421,7 @@ def main():
                           "parallelism": f"{world} independent instances (one per GPU)"},
                "summary_build_ms": phase["build_ms"] + phase["summary_ms"],
                "phases_ms": phase,
+               "phase_rooflines": phase_rooflines,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": int(prof["launches"]), "clocks": clk}
         print(json.dumps(out), flush=True)

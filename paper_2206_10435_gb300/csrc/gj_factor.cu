@@ -110,6 +110,45 @@ __global__ void k_group_compact(ColSet cs, const uint32_t *__restrict__ perm,
     if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
 }
 
+// Where each key column sits in the single packed word of a sorted key:
+// value = ((key >> shift) & (2^bits - 1)) + min.  Columns outside the
+// factor's order (projected away) are read through perm instead.
+struct UnpackSpec {
+    int ncol;
+    int col[MAX_KEYS];
+    int32_t mn[MAX_KEYS];
+    int shift[MAX_KEYS];
+    int bits[MAX_KEYS];
+    int nother;
+    int other_col[MAX_KEYS];
+    const int32_t *other[MAX_KEYS];
+};
+
+// group starts and key values from the sorted packed keys (no random reads
+// of the key columns)
+__global__ void k_group_compact_packed(UnpackSpec u, const uint64_t *__restrict__ keys,
+                                       const uint32_t *__restrict__ perm,
+                                       const uint8_t *__restrict__ head,
+                                       const uint32_t *__restrict__ gid, int64_t n, int64_t G,
+                                       uint32_t *gstart, int32_t *gkey) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        if (!head[i]) continue;
+        const uint32_t g = gid[i];
+        gstart[g] = (uint32_t)i;
+        const uint64_t k = keys[i];
+        for (int c = 0; c < u.ncol; c++) {
+            const uint64_t mask = u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << u.bits[c]) - 1);
+            const uint32_t v = (u.shift[c] < 64 ? (uint32_t)((k >> u.shift[c]) & mask) : 0u) + (uint32_t)u.mn[c];
+            gkey[(int64_t)u.col[c] * G + g] = (int32_t)v;
+        }
+        if (u.nother) {
+            const uint32_t r = perm[i];
+            for (int c = 0; c < u.nother; c++) gkey[(int64_t)u.other_col[c] * G + g] = u.other[c][r];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
+}
+
 // sorted[c*n + i] = col_c[perm[i]]: the key columns in sorted order, one
 // random read per column and row (used when the key spans several words)
 __global__ void k_gather_cols(ColSet cs, const uint32_t *__restrict__ perm, int64_t n,
@@ -294,8 +333,25 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
                                                                     F.gstart, F.gkey); c.launches++;
         dfree(c, sorted);
     } else {
-        k_group_compact<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, head, gid, n, F.G, F.gstart,
-                                                             F.gkey); c.launches++;
+        // one packed word: unpack the key values of every group head
+        UnpackSpec u{};
+        int shift = 0;
+        for (int col : words[0]) {   // least significant first, as packed
+            u.col[u.ncol] = col;
+            u.mn[u.ncol] = R.kmin[col];
+            u.shift[u.ncol] = shift;
+            u.bits[u.ncol] = bits[col];
+            shift += bits[col];
+            u.ncol++;
+        }
+        for (int col = 0; col < R.nk; col++) {
+            if (std::find(order.begin(), order.end(), col) != order.end()) continue;
+            u.other_col[u.nother] = col;
+            u.other[u.nother] = R.key[col];
+            u.nother++;
+        }
+        k_group_compact_packed<<<grid_for(c, n), FT, 0, c.stream>>>(u, keys, F.perm, head, gid, n, F.G,
+                                                                    F.gstart, F.gkey); c.launches++;
     }
     GJ_CUDA_TRY(cudaGetLastError());
     for (int p = 0; p < R.np; p++) {

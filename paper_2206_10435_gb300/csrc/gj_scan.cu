@@ -130,7 +130,30 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
             T agg_v = wh ? wv : op(pw_v, wv);
             uint32_t agg_h = wh | pw_h;
             T carry = T(0);
-            if (tile == 0) {
+            if constexpr (sizeof(T) == 4 && !SEG) {
+                // 32-bit values: flag and value share one 64-bit status word
+                // (the agg/inc area, 8 bytes per tile), published by one
+                // atomic store and read by one load, so no fences
+                unsigned long long *st = reinterpret_cast<unsigned long long *>(st_agg);
+                constexpr unsigned long long P_AGG = 1ull << 32, P_PREFIX = 2ull << 32;
+                if (tile == 0) {
+                    atomicExch(&st[0], P_PREFIX | (uint32_t)agg_v);
+                } else {
+                    atomicExch(&st[tile], P_AGG | (uint32_t)agg_v);
+                    int64_t p = (int64_t)tile - 1;
+                    while (p >= 0) {
+                        unsigned long long w;
+                        uint32_t spins = 0;
+                        while (((w = ld_volatile(&st[p])) >> 32) == 0) {
+                            if (++spins > SPIN_LIMIT) { raise_err(err, ERRF_TIMEOUT); w = P_PREFIX; break; }
+                        }
+                        carry = op((T)(uint32_t)w, carry);
+                        if (w & P_PREFIX) break;
+                        p--;
+                    }
+                    atomicExch(&st[tile], P_PREFIX | (uint32_t)op(carry, agg_v));
+                }
+            } else if (tile == 0) {
                 st_inc[tile] = agg_v;
                 __threadfence();
                 atomicExch(&st_flag[tile], F_PREFIX | (agg_h ? F_HEAD : 0u));
@@ -208,7 +231,8 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
     size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
     size_t bytes = 16 + flag_bytes + 2 * (size_t)tiles * sizeof(T);
     GJ_CUDA_TRY(dalloc_bytes(c, (void **)&state, bytes));
-    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 16 + flag_bytes, c.stream));
+    // 32-bit scans keep their status in the value area: clear it too
+    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, (sizeof(T) == 4 && !SEG) ? bytes : 16 + flag_bytes, c.stream));
     uint32_t *counter = state;
     uint32_t *flags = state + 4;
     T *agg = (T *)((char *)state + 16 + flag_bytes);
@@ -276,7 +300,8 @@ cudaError_t scan_u32_in(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32
     int64_t tiles = ceil_div(n, TILE);
     size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
     uint32_t *state = (uint32_t *)state_mem;
-    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 16 + flag_bytes, c.stream));
+    // the status words live in the value area (see k_scan): clear it too
+    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 16 + flag_bytes + 8 * (size_t)tiles, c.stream));
     uint32_t *counter = state;
     uint32_t *fl = state + 4;
     uint32_t *agg = (uint32_t *)((char *)state + 16 + flag_bytes);
