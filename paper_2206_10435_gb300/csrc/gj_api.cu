@@ -12,6 +12,7 @@ namespace gj {
 
 cudaError_t relation_minmax(Ctx &c, Relation &R);
 cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Factor &F);
+cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const std::vector<Factor *> &F);
 void factor_free(Ctx &c, Factor &F);
 void query_free_summary(Ctx &c, QueryState &q);
 gj_status summarize(QueryState &q, uint64_t *total_out);
@@ -345,6 +346,39 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
 
 namespace {
 
+// The factors of the query's relations (factor order: separator columns,
+// then the relation's own); the missing ones are built together, sharing
+// their host synchronisations.
+gj_status get_factors(CtxState &cs, std::vector<QRel> &ts) {
+    std::vector<std::vector<int>> orders(ts.size());
+    std::vector<Relation *> R;
+    std::vector<Factor *> F;
+    std::vector<std::unique_ptr<Factor>> made;
+    for (size_t i = 0; i < ts.size(); i++) {
+        orders[i] = ts[i].sep_cols;
+        orders[i].insert(orders[i].end(), ts[i].new_cols.begin(), ts[i].new_cols.end());
+        if (ts[i].R->factors.count(orders[i])) continue;
+        bool dup = false;
+        for (size_t k = 0; k < F.size() && !dup; k++) dup = R[k] == ts[i].R && F[k]->order == orders[i];
+        if (dup) continue;
+        made.emplace_back(new Factor());
+        made.back()->order = orders[i];
+        R.push_back(ts[i].R);
+        F.push_back(made.back().get());
+    }
+    if (!F.empty()) {
+        cudaError_t e = factor_build_many(cs.c, R, F);
+        gj_status st = e == cudaSuccess ? check_device_error(cs.c) : from_cuda(e);
+        if (st != GJ_OK) {
+            for (auto &f : made) factor_free(cs.c, *f);
+            return st;
+        }
+        for (size_t k = 0; k < made.size(); k++) R[k]->factors[F[k]->order] = std::move(made[k]);
+    }
+    for (size_t i = 0; i < ts.size(); i++) ts[i].F = ts[i].R->factors[orders[i]].get();
+    return GJ_OK;
+}
+
 // The cyclic 3-way join (gj_cycle.cu): three relations of two distinct key
 // attributes each, every pair sharing exactly one, the three shared
 // attributes distinct (R0(A,B), R1(B,C), R2(C,A) up to column order).  Fills
@@ -426,14 +460,8 @@ gj_status query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
     q.r.resize(n_rel);
     if (n_rel == 3 && drop.empty() && plan_triangle(ctx->s, rel_ids, q)) {
         DeviceGuard g(ctx->s.c.device);
-        for (int j = 0; j < 3; j++) {
-            QRel &t = q.r[j];
-            std::vector<int> order(t.sep_cols);
-            order.insert(order.end(), t.new_cols.begin(), t.new_cols.end());
-            gj_status st = GJ_OK;
-            t.F = get_factor(ctx->s, *t.R, order, &st);
-            if (!t.F) return st;
-        }
+        gj_status st = get_factors(ctx->s, q.r);
+        if (st != GJ_OK) return st;
         *out = qq.release();
         return GJ_OK;
     }
@@ -490,14 +518,8 @@ gj_status query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
     if (q.var_rel.size() > 32 || q.col_rel.size() > 32) return GJ_ERR_INVALID;
     // factors: separator columns lead, then the relation's own columns
     DeviceGuard g(ctx->s.c.device);
-    for (int j = 0; j < n_rel; j++) {
-        QRel &t = q.r[j];
-        std::vector<int> order(t.sep_cols);
-        order.insert(order.end(), t.new_cols.begin(), t.new_cols.end());
-        gj_status st = GJ_OK;
-        t.F = get_factor(ctx->s, *t.R, order, &st);
-        if (!t.F) return st;
-    }
+    gj_status st = get_factors(ctx->s, q.r);
+    if (st != GJ_OK) return st;
     *out = qq.release();
     return GJ_OK;
 }

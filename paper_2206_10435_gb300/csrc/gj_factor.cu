@@ -240,31 +240,49 @@ void factor_free(Ctx &c, Factor &F) {
     F.pay.clear();
 }
 
-cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Factor &F) {
-    F.order = order;
+namespace {
+
+// One factor build in two stages, so that the builds of several relations
+// share their host synchronisations: the key ranges (for the packed field
+// widths) before the sort, and the group counts (for the group arrays)
+// after it.
+struct FactorBuild {
+    Relation *R = nullptr;
+    Factor *F = nullptr;
+    std::vector<int> bits;
+    std::vector<std::vector<int>> words;
+    uint64_t *keys = nullptr;
+    uint8_t *head = nullptr;
+    uint32_t *gid = nullptr, *gcount = nullptr;
+    int32_t *sorted = nullptr;
+};
+
+void fb_free(Ctx &c, FactorBuild &b) {
+    dfree(c, b.keys);
+    dfree(c, b.head);
+    dfree(c, b.gid);
+    dfree(c, b.gcount);
+    dfree(c, b.sorted);
+}
+
+// stage 1 (key ranges known): rows sorted by the key tuple, group heads
+// marked and numbered; the group count lands in b.gcount
+cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
+    Relation &R = *b.R;
+    Factor &F = *b.F;
+    const std::vector<int> &order = F.order;
     F.n = R.n;
     const int64_t n = R.n;
-    GJ_CUDA_TRY(relation_minmax(c, R));
     GJ_CUDA_TRY(dalloc(c, &F.perm, n));
-    if (n == 0) {
-        F.G = 0;
-        GJ_CUDA_TRY(dalloc(c, &F.gstart, 1));
-        GJ_CUDA_TRY(cudaMemsetAsync(F.gstart, 0, sizeof(uint32_t), c.stream));
-        GJ_CUDA_TRY(dalloc(c, &F.gkey, 1));
-        for (int p = 0; p < R.np; p++) {
-            void *d = nullptr;
-            GJ_CUDA_TRY(dalloc_bytes(c, &d, 16));
-            F.pay.push_back(d);
-        }
-        return cudaSuccess;
-    }
+    if (n == 0) return cudaSuccess;
     // field widths, least significant column last in `order`
-    std::vector<int> bits(R.nk);
+    std::vector<int> &bits = b.bits;
+    bits.assign(R.nk, 0);
     for (int i = 0; i < R.nk; i++)
         bits[i] = bits_of((uint32_t)((int64_t)R.kmax[i] - (int64_t)R.kmin[i]));
     // cut the order into words of <= 64 bits, starting from the least
     // significant column
-    std::vector<std::vector<int>> words;
+    std::vector<std::vector<int>> &words = b.words;
     {
         std::vector<int> cur;
         int used = 0;
@@ -280,8 +298,8 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
         }
         if (!cur.empty()) words.push_back(cur);
     }
-    uint64_t *keys = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &keys, n));
+    GJ_CUDA_TRY(dalloc(c, &b.keys, n));
+    uint64_t *keys = b.keys;
     bool first = true;
     for (auto &wcols : words) {   // least significant word first
         PackSpec ps{};
@@ -299,15 +317,15 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
         GJ_CUDA_TRY(radix_sort_u64_u32(c, keys, F.perm, n, shift));
         first = false;
     }
-    uint8_t *head = nullptr;
-    uint32_t *gid = nullptr, *gcount = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &head, n));
-    GJ_CUDA_TRY(dalloc(c, &gid, n));
-    GJ_CUDA_TRY(dalloc(c, &gcount, 1));
+    GJ_CUDA_TRY(dalloc(c, &b.head, n));
+    GJ_CUDA_TRY(dalloc(c, &b.gid, n));
+    GJ_CUDA_TRY(dalloc(c, &b.gcount, 1));
+    uint8_t *head = b.head;
+    uint32_t *gid = b.gid, *gcount = b.gcount;
     ColSet all{};
     all.ncol = R.nk;
     for (int i = 0; i < R.nk; i++) all.col[i] = R.key[i];
-    int32_t *sorted = nullptr;
+    int32_t *&sorted = b.sorted;
     if (words.size() == 1) {
         k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(keys, n, head); c.launches++;
     } else {
@@ -322,10 +340,35 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
     }
     GJ_CUDA_TRY(cudaGetLastError());
     GJ_CUDA_TRY(scan_u32(c, nullptr, head, gid, n, gcount));
-    uint32_t *hg = (uint32_t *)c.pinned;
-    GJ_CUDA_TRY(cudaMemcpyAsync(hg, gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream));
-    GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    F.G = hg[0];
+    return cudaSuccess;
+}
+
+// stage 2 (group count G known): group starts and keys, payloads in group
+// order; frees the stage's temporaries
+cudaError_t fb_groups(Ctx &c, FactorBuild &b, int64_t G) {
+    Relation &R = *b.R;
+    Factor &F = *b.F;
+    const std::vector<int> &order = F.order;
+    const int64_t n = R.n;
+    if (n == 0) {
+        F.G = 0;
+        GJ_CUDA_TRY(dalloc(c, &F.gstart, 1));
+        GJ_CUDA_TRY(cudaMemsetAsync(F.gstart, 0, sizeof(uint32_t), c.stream));
+        GJ_CUDA_TRY(dalloc(c, &F.gkey, 1));
+        for (int p = 0; p < R.np; p++) {
+            void *d = nullptr;
+            GJ_CUDA_TRY(dalloc_bytes(c, &d, 16));
+            F.pay.push_back(d);
+        }
+        return cudaSuccess;
+    }
+    const std::vector<int> &bits = b.bits;
+    const std::vector<std::vector<int>> &words = b.words;
+    uint64_t *keys = b.keys;
+    uint8_t *head = b.head;
+    uint32_t *gid = b.gid;
+    int32_t *&sorted = b.sorted;
+    F.G = G;
     GJ_CUDA_TRY(dalloc(c, &F.gstart, F.G + 1));
     GJ_CUDA_TRY(dalloc(c, &F.gkey, (size_t)R.nk * F.G));
     if (sorted) {
@@ -367,11 +410,82 @@ cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Fac
         GJ_CUDA_TRY(cudaGetLastError());
         F.pay.push_back(d);
     }
-    dfree(c, keys);
-    dfree(c, head);
-    dfree(c, gid);
-    dfree(c, gcount);
+    fb_free(c, b);
     return cudaSuccess;
+}
+
+}  // namespace
+
+// Builds the factors F[i] (order set) of relations R[i] together: one
+// readback of every missing key range, the sorts, one readback of every
+// group count, then the group arrays.  On error the caller frees the
+// factors (factor_free); temporaries are freed here.
+cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const std::vector<Factor *> &F) {
+    const size_t m = R.size();
+    // key ranges of the relations that lack them, one readback
+    std::vector<Relation *> need;
+    for (Relation *r : R)
+        if (!r->have_minmax && std::find(need.begin(), need.end(), r) == need.end()) need.push_back(r);
+    size_t words_mm = 0;
+    for (Relation *r : need) words_mm += 2 * r->nk;
+    if (words_mm * 4 > (1 << 16) || m * 4 > (1 << 16)) return cudaErrorInvalidValue;
+    if (words_mm) {
+        int32_t *mm = nullptr;
+        GJ_CUDA_TRY(dalloc(c, &mm, words_mm));
+        size_t off = 0;
+        for (Relation *r : need) {
+            if (r->n > 0) {
+                ColSet cs{};
+                cs.ncol = r->nk;
+                for (int i = 0; i < r->nk; i++) cs.col[i] = r->key[i];
+                k_minmax_init<<<1, 32, 0, c.stream>>>(r->nk, mm + off); c.launches++;
+                dim3 grid((unsigned)std::max(1, grid_for(c, r->n) / std::max(1, r->nk)), r->nk);
+                k_minmax<<<grid, FT, 0, c.stream>>>(cs, r->n, mm + off); c.launches++;
+                GJ_CUDA_TRY(cudaGetLastError());
+            }
+            off += 2 * r->nk;
+        }
+        // device->host readbacks go through the pinned buffer, then sync
+        int32_t *h = (int32_t *)c.pinned;
+        GJ_CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(int32_t) * words_mm, cudaMemcpyDeviceToHost, c.stream));
+        GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        off = 0;
+        for (Relation *r : need) {
+            r->kmin.assign(r->nk, 0);
+            r->kmax.assign(r->nk, 0);
+            if (r->n > 0)
+                for (int i = 0; i < r->nk; i++) { r->kmin[i] = h[off + 2 * i]; r->kmax[i] = h[off + 2 * i + 1]; }
+            r->have_minmax = true;
+            off += 2 * r->nk;
+        }
+        dfree(c, mm);
+    }
+    std::vector<FactorBuild> b(m);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < m && e == cudaSuccess; i++) {
+        b[i].R = R[i];
+        b[i].F = F[i];
+        e = fb_sort(c, b[i]);
+    }
+    // group counts, one readback
+    uint32_t *hg = (uint32_t *)c.pinned;
+    for (size_t i = 0; i < m && e == cudaSuccess; i++)
+        if (b[i].gcount) e = cudaMemcpyAsync(hg + i, b[i].gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    std::vector<int64_t> G(m, 0);
+    if (e == cudaSuccess)
+        for (size_t i = 0; i < m; i++) G[i] = b[i].gcount ? (int64_t)hg[i] : 0;
+    for (size_t i = 0; i < m && e == cudaSuccess; i++) e = fb_groups(c, b[i], G[i]);
+    if (e != cudaSuccess) {
+        note_cuda_error(e, __FILE__, __LINE__);
+        for (auto &x : b) fb_free(c, x);
+    }
+    return e;
+}
+
+cudaError_t factor_build(Ctx &c, Relation &R, const std::vector<int> &order, Factor &F) {
+    F.order = order;
+    return factor_build_many(c, {&R}, {&F});
 }
 
 }  // namespace gj
