@@ -49,6 +49,34 @@ __device__ __forceinline__ void st_cs_32B(unsigned int *p, const unsigned int (&
                  "r"(v[7]) : "memory");
 }
 
+// Loads with an L2 eviction priority (createpolicy + L2::cache_hint): the
+// factors' arrays (group starts, keys, payloads, row ids) are gathered
+// again and again and should stay in L2; the block list is read once and
+// should leave first, as should the result columns (streaming stores).
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_once() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ unsigned int ld_hint(const unsigned int *a, uint64_t pol) {
+    unsigned int v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int ld_hint(const int *a, uint64_t pol) {
+    return (int)ld_hint((const unsigned int *)a, pol);
+}
+__device__ __forceinline__ unsigned long long ld_hint(const unsigned long long *a, uint64_t pol) {
+    unsigned long long v;
+    asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
 // all lanes of the warp must call this (shuffles)
 template <int RPT, class T>
 __device__ __forceinline__ void emit_store_col(const T (&v)[RPT], T *dst, int64_t rbeg, int nrow,
@@ -109,7 +137,9 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
         if (threadIdx.x == 0) raise_err(e.err, ERRF_BOUNDS);
         return;
     }
-    for (int t = threadIdx.x; t < nb; t += EMIT_DT) s_A[t] = e.A[first + t];
+    const uint64_t keep = policy_keep(), once = policy_once();
+    for (int t = threadIdx.x; t < nb; t += EMIT_DT)
+        s_A[t] = ld_hint((const unsigned long long *)e.A + first + t, once);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t rbeg = r0 + (int64_t)threadIdx.x * RPT;
@@ -145,7 +175,7 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
     for (int i = 0; i < RPT; i++)
 #pragma unroll
         for (int j = 0; j < K; j++)
-            g[i][j] = nb_row[i] ? __ldg(e.grp[j] + first + lb[i]) : g[i > 0 ? i - 1 : 0][j];
+            g[i][j] = nb_row[i] ? ld_hint(e.grp[j] + first + lb[i], once) : g[i > 0 ? i - 1 : 0][j];
     // key columns need only the groups: write them while extents load
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -155,7 +185,7 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
             unsigned int v[RPT];
 #pragma unroll
             for (int i = 0; i < RPT; i++)
-                v[i] = nb_row[i] ? __ldg(src + g[i][j]) : v[i > 0 ? i - 1 : 0];
+                v[i] = nb_row[i] ? ld_hint(src + g[i][j], keep) : v[i > 0 ? i - 1 : 0];
             emit_store_col<RPT>(v, (unsigned int *)e.dst[c], rbeg, nrow, g32, e.vec, lane);
         }
     }
@@ -167,8 +197,8 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
 #pragma unroll
             for (int j = 0; j < K; j++) {
                 if (nb_row[i]) {
-                    base[i][j] = __ldg(e.gstart[j] + g[i][j]);
-                    cnt[i][j] = __ldg(e.gstart[j] + g[i][j] + 1) - base[i][j];
+                    base[i][j] = ld_hint(e.gstart[j] + g[i][j], keep);
+                    cnt[i][j] = ld_hint(e.gstart[j] + g[i][j] + 1, keep) - base[i][j];
                 } else {
                     base[i][j] = base[i > 0 ? i - 1 : 0][j];
                     cnt[i][j] = cnt[i > 0 ? i - 1 : 0][j];
@@ -220,20 +250,20 @@ k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, cons
                 const unsigned long long *src = (const unsigned long long *)e.src[c];
                 unsigned long long v[RPT];
 #pragma unroll
-                for (int i = 0; i < RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                for (int i = 0; i < RPT; i++) v[i] = ld_hint(src + pos[i][j], keep);
                 emit_store_col<RPT>(v, (unsigned long long *)e.dst[c], rbeg, nrow, g64, e.vec, lane);
             } else if (kind == 1) {
                 const unsigned int *src = (const unsigned int *)e.src[c];
                 unsigned int v[RPT];
 #pragma unroll
-                for (int i = 0; i < RPT; i++) v[i] = __ldg(src + pos[i][j]);
+                for (int i = 0; i < RPT; i++) v[i] = ld_hint(src + pos[i][j], keep);
                 emit_store_col<RPT>(v, (unsigned int *)e.dst[c], rbeg, nrow, g32, e.vec, lane);
             }
         }
         if (e.rid_out[j]) {
             unsigned int v[RPT];
 #pragma unroll
-            for (int i = 0; i < RPT; i++) v[i] = __ldg(e.perm[j] + pos[i][j]);
+            for (int i = 0; i < RPT; i++) v[i] = ld_hint(e.perm[j] + pos[i][j], keep);
             emit_store_col<RPT>(v, e.rid_out[j], rbeg, nrow, g32,
                                 e.vec && ((uintptr_t)e.rid_out[j] & 31) == 0, lane);
         }
