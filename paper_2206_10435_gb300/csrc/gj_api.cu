@@ -52,7 +52,10 @@ struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
         cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
+        // always: in a thread that has not used CUDA yet this also makes the
+        // device's primary context current (cudaGetDevice alone reports
+        // device 0 without doing so, and pointer queries then fail)
+        cudaSetDevice(dev);
     }
     ~DeviceGuard() {
         int cur = -1;
@@ -649,25 +652,40 @@ gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows, void *cons
     // every column must be addressable by the device: its own memory,
     // managed memory, or pinned host memory (translated to the device's
     // address for it)
-    auto device_view = [&](void *p, void **dv) -> bool {
+    // (a rejected column is described in gj_last_error)
+    auto device_view = [&](void *p, void **dv, const char *what, size_t idx) -> bool {
         cudaPointerAttributes at{};
-        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-        if (at.type == cudaMemoryTypeDevice) { *dv = p; return at.device == device; }
+        cudaError_t e = cudaPointerGetAttributes(&at, p);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(g_last_error, sizeof(g_last_error), "%s %zu: cudaPointerGetAttributes: %s", what,
+                     idx, cudaGetErrorName(e));
+            return false;
+        }
+        if (at.type == cudaMemoryTypeDevice && at.device == device) { *dv = p; return true; }
         if (at.type == cudaMemoryTypeManaged) { *dv = p; return true; }
         if (at.type == cudaMemoryTypeHost && at.devicePointer) { *dv = at.devicePointer; return true; }
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "%s %zu: memory type %d (device %d, device address %p) is not addressable by device %d",
+                 what, idx, (int)at.type, at.device, at.devicePointer, device);
         return false;
     };
     const size_t ncols = q->s.var_rel.size() + q->s.col_rel.size();
     std::vector<void *> cols(ncols);
-    for (size_t i = 0; i < ncols; i++)
-        if (!out_cols[i] || !device_view(out_cols[i], &cols[i])) return GJ_ERR_INVALID;
+    for (size_t i = 0; i < ncols; i++) {
+        if (!out_cols[i]) {
+            snprintf(g_last_error, sizeof(g_last_error), "output column %zu is NULL", i);
+            return GJ_ERR_INVALID;
+        }
+        if (!device_view(out_cols[i], &cols[i], "output column", i)) return GJ_ERR_INVALID;
+    }
     std::vector<uint32_t *> rids;
     if (rowid_cols) {
         rids.assign(q->s.k, nullptr);
         for (int j = 0; j < q->s.k; j++) {
             if (!rowid_cols[j]) continue;
             void *dv = nullptr;
-            if (!device_view(rowid_cols[j], &dv)) return GJ_ERR_INVALID;
+            if (!device_view(rowid_cols[j], &dv, "row-id column", (size_t)j)) return GJ_ERR_INVALID;
             rids[j] = (uint32_t *)dv;
         }
     }

@@ -30,8 +30,10 @@ class GJError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
         msg = f"{what}: {_lib.gj_status_str(status).decode()} (status {status})"
-        if status == GJ_ERR_CUDA:
-            msg += f" [{_lib.gj_last_error().decode()}]"
+        if status in (GJ_ERR_CUDA, GJ_ERR_INVALID):
+            last = _lib.gj_last_error().decode()
+            if last:
+                msg += f" [{last}]"
         super().__init__(msg)
 
 

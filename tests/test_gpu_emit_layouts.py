@@ -155,3 +155,40 @@ def test_pageable_columns_rejected(kctx):
         assert torch.equal(a, b)
     assert total > 0
     run.close()
+
+
+def test_pinned_host_columns_from_fresh_threads(kctx):
+    """Two host threads that have not used CUDA before desummarise alternate
+    windows of two queries (own streams) into pinned host columns."""
+    import threading
+    q = one_payload(G.random_tree_query(1207, 4, max_rows=60, domain=6, max_new=2,
+                                        min_rows=20), "i64")
+    run = Run(kctx, q)
+    total = run.summarize()
+    ref, _ = run.q.desummarize(0, total, rowids=True)
+    ref = [c.cpu() for c in ref]
+    qs = [kctx.query(run.ids) for _ in range(2)]
+    for qq in qs:
+        qq.set_stream(torch.cuda.Stream())
+        assert qq.summarize() == total
+    W = 1000
+    errs = []
+
+    def work(k):
+        try:
+            for r0 in range(k * W, total, 2 * W):
+                host = [torch.empty(W, dtype=c.dtype, pin_memory=True) for c in ref]
+                got = qs[k].desummarize(r0, W, out=host)
+                for a, b in zip(got, ref):
+                    assert torch.equal(a, b[r0:r0 + a.shape[0]])
+        except Exception as e:   # reported on the main thread
+            errs.append(e)
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for qq in qs:
+        qq.close()
+    run.close()
