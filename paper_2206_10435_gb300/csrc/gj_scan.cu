@@ -35,6 +35,90 @@ struct SatAddU64 {
 template <class T>
 __device__ __forceinline__ T ld_volatile(const T *p) { return *(const volatile T *)p; }
 
+// Tile status of the unsegmented scans: a flag (ST_A: the tile's aggregate
+// is published, ST_P: its inclusive prefix is) and the value, written and
+// read as one word so that a reader never pairs a flag with another
+// publication's value and no memory fence is needed.  32-bit values share
+// an 8-byte word with the flag; 64-bit values take a 16-byte aligned pair
+// moved by one vector access.
+constexpr uint32_t ST_A = 1u, ST_P = 2u;
+
+template <class T> struct TileStatus;
+template <> struct TileStatus<uint32_t> {
+    using W = unsigned long long;
+    static __device__ __forceinline__ void put(W *s, uint32_t f, uint32_t v) {
+        atomicExch(s, ((W)f << 32) | v);
+    }
+    static __device__ __forceinline__ void get(const W *s, uint32_t &f, uint32_t &v) {
+        const W w = ld_volatile(s);
+        f = (uint32_t)(w >> 32);
+        v = (uint32_t)w;
+    }
+};
+template <> struct TileStatus<uint64_t> {
+    using W = ulonglong2;
+    static __device__ __forceinline__ void put(W *s, uint32_t f, uint64_t v) {
+        asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(s), "l"((unsigned long long)f),
+                     "l"((unsigned long long)v)
+                     : "memory");
+    }
+    static __device__ __forceinline__ void get(const W *s, uint32_t &f, uint64_t &v) {
+        unsigned long long a, b;
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(s) : "memory");
+        f = (uint32_t)a;
+        v = b;
+    }
+};
+
+// Decoupled lookback by one warp: publishes the tile's aggregate, then
+// reads the status of 32 predecessors at a time (lane 31 the nearest),
+// folds everything from the nearest published prefix onwards, and moves 32
+// tiles further back only while all of them hold just an aggregate.
+// Returns the tile's carry-in (the same in every lane) after publishing its
+// inclusive prefix.  Op must be associative and commutative (the window is
+// folded by a butterfly).  Every poll is bounded: on expiry ERRF_TIMEOUT is
+// recorded and the predecessor counts as a zero prefix.
+template <class T, class Op>
+__device__ __forceinline__ T warp_lookback(typename TileStatus<T>::W *st, uint32_t tile, T agg,
+                                           int lane, uint32_t *err) {
+    Op op;
+    if (tile == 0) {
+        if (lane == 0) TileStatus<T>::put(&st[0], ST_P, agg);
+        return T(0);
+    }
+    if (lane == 0) TileStatus<T>::put(&st[tile], ST_A, agg);
+    T carry = T(0);
+    int64_t p = (int64_t)tile - 1;
+    for (;;) {
+        const int64_t q = p - 31 + lane;
+        uint32_t f = ST_P;   // tiles before the first count as a zero prefix
+        T v = T(0);
+        if (q >= 0) {
+            uint32_t spins = 0;
+            for (;;) {
+                TileStatus<T>::get(&st[q], f, v);
+                if (f) break;
+                if (++spins > SPIN_LIMIT) {
+                    raise_err(err, ERRF_TIMEOUT);
+                    f = ST_P;
+                    v = T(0);
+                    break;
+                }
+            }
+        }
+        const uint32_t pm = __ballot_sync(0xffffffffu, f == ST_P);
+        const int hi = pm ? 31 - __clz((int)pm) : 0;
+        T x = lane >= hi ? v : T(0);
+#pragma unroll
+        for (int d = 16; d; d >>= 1) x = op(x, __shfl_xor_sync(0xffffffffu, x, d));
+        carry = op(x, carry);
+        if (pm) break;
+        p -= 32;
+    }
+    if (lane == 0) TileStatus<T>::put(&st[tile], ST_P, op(carry, agg));
+    return carry;
+}
+
 template <class T, class Op, int ITEMS, bool SEG, bool PERSIST>
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
@@ -126,34 +210,21 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
         uint32_t th_h = ex_h | pw_h;
 
         // tile aggregate and lookback
-        if (tid == SCAN_THREADS - 1) {
+        if constexpr (!SEG) {
+            if (warp == SCAN_THREADS / 32 - 1) {
+                const T agg_v = __shfl_sync(0xffffffffu, op(pw_v, wv), 31);
+                const T carry = warp_lookback<T, Op>(
+                    reinterpret_cast<typename TileStatus<T>::W *>(st_agg), tile, agg_v, lane, err);
+                if (lane == 31) {
+                    s_carry = carry;
+                    if (total && base + TILE >= n) *total = op(carry, agg_v);
+                }
+            }
+        } else if (tid == SCAN_THREADS - 1) {
             T agg_v = wh ? wv : op(pw_v, wv);
             uint32_t agg_h = wh | pw_h;
             T carry = T(0);
-            if constexpr (sizeof(T) == 4 && !SEG) {
-                // 32-bit values: flag and value share one 64-bit status word
-                // (the agg/inc area, 8 bytes per tile), published by one
-                // atomic store and read by one load, so no fences
-                unsigned long long *st = reinterpret_cast<unsigned long long *>(st_agg);
-                constexpr unsigned long long P_AGG = 1ull << 32, P_PREFIX = 2ull << 32;
-                if (tile == 0) {
-                    atomicExch(&st[0], P_PREFIX | (uint32_t)agg_v);
-                } else {
-                    atomicExch(&st[tile], P_AGG | (uint32_t)agg_v);
-                    int64_t p = (int64_t)tile - 1;
-                    while (p >= 0) {
-                        unsigned long long w;
-                        uint32_t spins = 0;
-                        while (((w = ld_volatile(&st[p])) >> 32) == 0) {
-                            if (++spins > SPIN_LIMIT) { raise_err(err, ERRF_TIMEOUT); w = P_PREFIX; break; }
-                        }
-                        carry = op((T)(uint32_t)w, carry);
-                        if (w & P_PREFIX) break;
-                        p--;
-                    }
-                    atomicExch(&st[tile], P_PREFIX | (uint32_t)op(carry, agg_v));
-                }
-            } else if (tile == 0) {
+            if (tile == 0) {
                 st_inc[tile] = agg_v;
                 __threadfence();
                 atomicExch(&st_flag[tile], F_PREFIX | (agg_h ? F_HEAD : 0u));
@@ -173,7 +244,7 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
                     __threadfence();
                     T v = (f & F_PREFIX) ? ld_volatile(&st_inc[p]) : ld_volatile(&st_agg[p]);
                     carry = op(v, carry);
-                    if ((f & F_PREFIX) || (SEG && (f & F_HEAD))) break;
+                    if ((f & F_PREFIX) || (f & F_HEAD)) break;
                     p--;
                 }
                 T inc = agg_h ? agg_v : op(carry, agg_v);
@@ -231,8 +302,8 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
     size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
     size_t bytes = 16 + flag_bytes + 2 * (size_t)tiles * sizeof(T);
     GJ_CUDA_TRY(dalloc_bytes(c, (void **)&state, bytes));
-    // 32-bit scans keep their status in the value area: clear it too
-    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, (sizeof(T) == 4 && !SEG) ? bytes : 16 + flag_bytes, c.stream));
+    // unsegmented scans keep their status words in the value area: clear it too
+    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, !SEG ? bytes : 16 + flag_bytes, c.stream));
     uint32_t *counter = state;
     uint32_t *flags = state + 4;
     T *agg = (T *)((char *)state + 16 + flag_bytes);
