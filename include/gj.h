@@ -121,8 +121,16 @@ gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
  * emit kernel writes, 2, 4 or 8 (default 4): fewer rows per thread means fewer
  * registers and more threads in flight, more rows means fewer block
  * lookups per row.  Takes effect for queries created afterwards.
+ * GJ_OPT_TRIANGLE_INTERSECT: how the cyclic 3-way join finds the group
+ * triples of its maxclique potential (Section 3.2.1): 0 (default) chooses
+ * by the key ranges and segment lengths, 1 sorted-list intersection,
+ * 2 bitmaps over C's value range (rows per value of B in S and of A in T;
+ * used only while they take at most 512 MiB, else lists).  The triples and
+ * their order are the same either way.  Takes effect at the next
+ * gj_summarize.
  */
 #define GJ_OPT_EMIT_ROWS_PER_THREAD 1
+#define GJ_OPT_TRIANGLE_INTERSECT 2
 gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value);
 
 /*

@@ -197,6 +197,11 @@ gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value) {
         ctx->s.c.emit_rpt = (int)value;
         return GJ_OK;
     }
+    if (option == GJ_OPT_TRIANGLE_INTERSECT) {
+        if (value < 0 || value > 2) return GJ_ERR_INVALID;
+        ctx->s.c.tri_mode = (int)value;
+        return GJ_OK;
+    }
     return GJ_ERR_INVALID;
 }
 
@@ -570,6 +575,7 @@ gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
         o->pool = base.pool;
         o->num_sms = base.num_sms;
         o->emit_rpt = base.emit_rpt;
+        o->tri_mode = base.tri_mode;
         if (cudaMalloc((void **)&o->err, 16) != cudaSuccess ||
             cudaMallocHost((void **)&o->pinned, 1 << 16) != cudaSuccess) {
             cudaGetLastError();

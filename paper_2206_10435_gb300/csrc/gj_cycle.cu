@@ -25,6 +25,15 @@
 //     a saturating scan gives the blocks' first rows and |Q|.
 // R groups come in R's order and each one's triples in c order, so blocks
 // are ordered by (V_0, V_1, c) with V the root's columns then C.
+//
+// When C's value range is small next to the segments, the same triples come
+// from bitmaps instead: one row per b holding S's c values, one row per a
+// holding T's; an R group's triples are the set bits of the AND of its two
+// rows, in c order, and a bit's rank among its row's set bits is the group's
+// offset inside the segment.  Each lane takes one 32-bit word of the AND per
+// step; output slots are handed to lanes in order (a search over the
+// lanes' prefix counts, then a select of the bit), so the writes stay
+// contiguous.
 #include <string.h>
 
 #include <algorithm>
@@ -102,6 +111,132 @@ __device__ __forceinline__ bool tri_match(const TriSpec &s, bool walk_s, uint32_
 }
 
 constexpr int TRI_WARPS = CT / 32;
+
+// Bitmap form of S and T (rows of `words` 32-bit words; bit c - cmin of
+// row x set iff the relation has the group (x + row min, c)); seg_* hold
+// the first group of each row that has one.
+struct TriBits {
+    const uint32_t *bs, *bt;
+    const uint32_t *seg_s, *seg_t;
+    int32_t bmin, bmax;   // S's B values: rows of bs
+    int32_t amin, amax;   // T's A values: rows of bt
+    uint32_t words;
+};
+
+// rows of one relation's bitmap from its groups (ordered by row key, then c)
+__global__ void k_tri_bitmap(const int32_t *__restrict__ row_key, const int32_t *__restrict__ c_key,
+                             int64_t G, int32_t rmin, int32_t cmin, uint32_t words, uint32_t *bm,
+                             uint32_t *seg) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t rk = row_key[g];
+        const uint32_t r = (uint32_t)((int64_t)rk - rmin);
+        const uint32_t c = (uint32_t)((int64_t)c_key[g] - cmin);
+        atomicOr(&bm[(size_t)r * words + (c >> 5)], 1u << (c & 31));
+        if (g == 0 || row_key[g - 1] != rk) seg[r] = (uint32_t)g;
+    }
+}
+
+// position of the r-th (from 0) set bit of m, which has more than r
+__device__ __forceinline__ uint32_t select_bit(uint32_t m, uint32_t r) {
+    uint32_t pos = 0;
+#pragma unroll
+    for (int w = 16; w; w >>= 1) {
+        const uint32_t lo = __popc(m & ((1u << w) - 1u));
+        if (r >= lo) {
+            r -= lo;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// exclusive warp prefix sum of x; *total gets the warp's sum
+__device__ __forceinline__ uint32_t warp_excl(uint32_t x, int lane, uint32_t *total) {
+    uint32_t v = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += y;
+    }
+    *total = __shfl_sync(0xffffffffu, v, 31);
+    return v - x;
+}
+
+// one warp per R group: pass WRITE=false counts its triples (cnt, total),
+// WRITE=true writes its blocks from base[i] on, in c order
+template <bool WRITE>
+__global__ void k_tri_bits(TriSpec s, TriBits t, uint32_t *cnt, unsigned long long *total,
+                           const uint32_t *__restrict__ base, uint32_t *g0, uint32_t *g1, uint32_t *g2,
+                           uint64_t *W) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * TRI_WARPS + (threadIdx.x >> 5); i < s.G0;
+         i += (int64_t)gridDim.x * TRI_WARPS) {
+        const int32_t a = s.a0[i], b = s.b0[i];
+        uint32_t hits = 0;
+        if (b >= t.bmin && b <= t.bmax && a >= t.amin && a <= t.amax) {
+            const uint32_t rb = (uint32_t)((int64_t)b - t.bmin), ra = (uint32_t)((int64_t)a - t.amin);
+            const uint32_t *rs = t.bs + (size_t)rb * t.words, *rt = t.bt + (size_t)ra * t.words;
+            if (!WRITE) {
+                for (uint32_t w = lane; w < t.words; w += 32) hits += __popc(rs[w] & rt[w]);
+            } else {
+                const uint32_t js = t.seg_s[rb], jt = t.seg_t[ra];
+                const uint64_t c0 = s.gs0[i + 1] - s.gs0[i];
+                uint32_t at = base[i], sr = 0, tr = 0;   // slots, S bits, T bits so far
+                for (uint32_t w0 = 0; w0 < t.words; w0 += 32) {
+                    const uint32_t w = w0 + lane;
+                    const uint32_t sw = w < t.words ? rs[w] : 0u, tw = w < t.words ? rt[w] : 0u;
+                    const uint32_t x = sw & tw;
+                    uint32_t ns, nt, nx;
+                    const uint32_t es = warp_excl(__popc(sw), lane, &ns);
+                    const uint32_t et = warp_excl(__popc(tw), lane, &nt);
+                    const uint32_t ex = warp_excl(__popc(x), lane, &nx);
+                    for (uint32_t o0 = 0; o0 < nx; o0 += 32) {
+                        const uint32_t o = o0 + lane;
+                        // the lane whose word holds slot o: the last one with ex <= o
+                        uint32_t L = 0;
+#pragma unroll
+                        for (int st = 16; st; st >>= 1) {
+                            const uint32_t e = __shfl_sync(0xffffffffu, ex, L + st);
+                            if (e <= o) L += st;
+                        }
+                        const uint32_t xL = __shfl_sync(0xffffffffu, x, L);
+                        const uint32_t exL = __shfl_sync(0xffffffffu, ex, L);
+                        const uint32_t swL = __shfl_sync(0xffffffffu, sw, L);
+                        const uint32_t esL = __shfl_sync(0xffffffffu, es, L);
+                        const uint32_t twL = __shfl_sync(0xffffffffu, tw, L);
+                        const uint32_t etL = __shfl_sync(0xffffffffu, et, L);
+                        if (o < nx) {
+                            const uint32_t bit = select_bit(xL, o - exL);
+                            const uint32_t below = (1u << bit) - 1u;
+                            const uint32_t j = js + sr + esL + __popc(swL & below);
+                            const uint32_t k = jt + tr + etL + __popc(twL & below);
+                            const uint32_t slot = at + o;
+                            g0[slot] = (uint32_t)i;
+                            g1[slot] = j;
+                            g2[slot] = k;
+                            const uint64_t c1 = s.gs1[j + 1] - s.gs1[j], c2 = s.gs2[k + 1] - s.gs2[k];
+                            W[slot] = sat_mul(sat_mul(c0, c1), c2);
+                        }
+                    }
+                    at += nx;
+                    sr += ns;
+                    tr += nt;
+                }
+            }
+        }
+        if (!WRITE) {
+            hits = __reduce_add_sync(0xffffffffu, hits);
+            if (lane == 0) {
+                cnt[i] = hits;
+                mine += hits;
+            }
+        }
+    }
+    if (!WRITE && lane == 0 && mine) atomicAdd(total, mine);
+}
 
 // pass 1: triples per R group (a warp per group) and their exact total
 __global__ void k_tri_count(TriSpec s, uint32_t *cnt, unsigned long long *total) {
@@ -195,6 +330,37 @@ TriSpec tri_spec(QueryState &q) {
     return s;
 }
 
+// Bitmap plan for the query's factors, or false when the lists are the
+// better (or the only affordable) form.  mode: 0 chooses, 1 lists, 2 bitmaps
+// when they fit.
+constexpr int64_t TRI_BITS_BYTES = 512ll << 20;
+
+bool tri_bits_plan(QueryState &q, const TriSpec &s, int mode, TriBits &t, int64_t &rows_s,
+                   int64_t &rows_t) {
+    if (mode == 1) return false;
+    const Relation &RS = *q.r[1].R, &RT = *q.r[2].R;
+    const int sb = q.tri_col[1][0], sc = q.tri_col[1][1];
+    const int tc = q.tri_col[2][0], ta = q.tri_col[2][1];
+    rows_s = (int64_t)RS.kmax[sb] - RS.kmin[sb] + 1;
+    rows_t = (int64_t)RT.kmax[ta] - RT.kmin[ta] + 1;
+    const int64_t cmin = std::min(RS.kmin[sc], RT.kmin[tc]), cmax = std::max(RS.kmax[sc], RT.kmax[tc]);
+    const int64_t words = (cmax - cmin + 1 + 31) / 32;
+    if ((rows_s + rows_t) * (words + 1) * 4 > TRI_BITS_BYTES) return false;
+    if (mode == 0) {
+        // a warp step of the bitmaps covers 1024 values of c; one of the lists
+        // covers 32 groups of the shorter segment, each with a binary search
+        const double seg_s = (double)s.G1 / (double)rows_s, seg_t = (double)s.G2 / (double)rows_t;
+        if ((double)((words + 31) / 32) > 1.0 + std::min(seg_s, seg_t) / 8.0) return false;
+    }
+    t.bmin = RS.kmin[sb];
+    t.bmax = RS.kmax[sb];
+    t.amin = RT.kmin[ta];
+    t.amax = RT.kmax[ta];
+    t.words = (uint32_t)words;
+    (void)cmax;
+    return true;
+}
+
 }  // namespace
 
 void tri_free(Ctx &c, QueryState &q) {
@@ -209,7 +375,11 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
     q.summarized = false;
     const TriSpec s = tri_spec(q);
     uint32_t *hits = nullptr, *base = nullptr, *cnt = nullptr;
+    uint32_t *bm = nullptr, *seg = nullptr;
     uint64_t *W = nullptr, *total_dev = nullptr;
+    TriBits tb{};
+    int64_t rows_s = 0, rows_t = 0;
+    bool bits = false;
     unsigned long long *tsum = nullptr;
     unsigned long long nb = 0;
     uint64_t total = 0;
@@ -217,6 +387,9 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
     cudaError_t e = cudaSuccess;
     const int64_t warps_grid = std::max<int64_t>(
         1, std::min<int64_t>(ceil_div(s.G0, TRI_WARPS), (int64_t)c.num_sms * 16));
+    auto groups_grid = [&](int64_t n) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, CT), (int64_t)c.num_sms * 16));
+    };
 #define TRY(x)                                                 \
     do {                                                       \
         e = (x);                                               \
@@ -233,7 +406,29 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
         // triples per R group, placed by a scan
         TRY(dalloc(c, &hits, s.G0));
         TRY(dalloc(c, &base, s.G0));
-        k_tri_count<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, hits, tsum); c.launches++;
+        bits = tri_bits_plan(q, s, c.tri_mode, tb, rows_s, rows_t);
+        if (bits) {
+            const size_t nbits = (size_t)(rows_s + rows_t) * tb.words;
+            TRY(dalloc(c, &bm, nbits));
+            TRY(dalloc(c, &seg, (size_t)(rows_s + rows_t)));
+            TRY(cudaMemsetAsync(bm, 0, nbits * 4, c.stream));
+            TRY(cudaMemsetAsync(seg, 0, (size_t)(rows_s + rows_t) * 4, c.stream));
+            const Relation &RS = *q.r[1].R, &RT = *q.r[2].R;
+            const int32_t cmin = std::min(RS.kmin[q.tri_col[1][1]], RT.kmin[q.tri_col[2][0]]);
+            tb.bs = bm;
+            tb.bt = bm + (size_t)rows_s * tb.words;
+            tb.seg_s = seg;
+            tb.seg_t = seg + rows_s;
+            k_tri_bitmap<<<groups_grid(s.G1), CT, 0, c.stream>>>(s.b1, s.c1, s.G1, tb.bmin, cmin, tb.words,
+                                                                  bm, seg); c.launches++;
+            k_tri_bitmap<<<groups_grid(s.G2), CT, 0, c.stream>>>(s.a2, s.c2, s.G2, tb.amin, cmin, tb.words,
+                                                                  bm + (size_t)rows_s * tb.words,
+                                                                  seg + rows_s); c.launches++;
+            k_tri_bits<false><<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, tb, hits, tsum, nullptr, nullptr,
+                                                                        nullptr, nullptr, nullptr); c.launches++;
+        } else {
+            k_tri_count<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, hits, tsum); c.launches++;
+        }
         TRY(cudaGetLastError());
         TRY(readback(c, tsum, &nb, 8));
         // blocks are numbered in 32 bits
@@ -243,8 +438,13 @@ gj_status tri_summarize(QueryState &q, uint64_t *total_out) {
             for (auto &g : q.blk_grp) TRY(dalloc(c, &g, nb));
             TRY(dalloc(c, &W, nb));
             TRY(dalloc(c, &q.blk_A, nb));
-            k_tri_blocks<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, base, q.blk_grp[0], q.blk_grp[1],
-                                                                    q.blk_grp[2], W); c.launches++;
+            if (bits)
+                k_tri_bits<true><<<(unsigned)warps_grid, CT, 0, c.stream>>>(
+                    s, tb, nullptr, nullptr, base, q.blk_grp[0], q.blk_grp[1], q.blk_grp[2], W);
+            else
+                k_tri_blocks<<<(unsigned)warps_grid, CT, 0, c.stream>>>(s, base, q.blk_grp[0], q.blk_grp[1],
+                                                                        q.blk_grp[2], W);
+            c.launches++;
             TRY(cudaGetLastError());
             TRY(scan_u64_sat(c, W, nullptr, q.blk_A, (int64_t)nb, total_dev, nullptr, nullptr));
             TRY(readback(c, total_dev, &total, 8));
@@ -266,6 +466,8 @@ done:
     if (!q.summarized) tri_free(c, q);
     dfree(c, hits);
     dfree(c, base);
+    dfree(c, bm);
+    dfree(c, seg);
     dfree(c, cnt);
     dfree(c, W);
     dfree(c, total_dev);

@@ -57,6 +57,7 @@ struct Ctx {
     int num_sms = 0;
     uint64_t launches = 0;            // kernels launched (profiling)
     int emit_rpt = 4;                 // result rows per thread of the emit kernel (2 or 4)
+    int tri_mode = 0;                 // triangle intersection: 0 chooses, 1 sorted lists, 2 bitmaps
     // device-time profile of the emit kernel (CUDA events on the stream)
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_used;     // emit kernel: start/stop pairs

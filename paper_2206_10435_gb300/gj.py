@@ -23,6 +23,7 @@ GJ_OK, GJ_ERR_INVALID, GJ_ERR_NOT_ACYCLIC, GJ_ERR_OOM, GJ_ERR_OVERFLOW, GJ_ERR_C
     GJ_ERR_TIMEOUT, GJ_ERR_STATE, GJ_ERR_CAPACITY = range(9)
 GJ_REL_BORROW, GJ_REL_COPY, GJ_REL_HOST = 0, 1, 2
 GJ_OPT_EMIT_ROWS_PER_THREAD = 1
+GJ_OPT_TRIANGLE_INTERSECT = 2   # 0 chooses, 1 sorted lists, 2 bitmaps
 SAT = (1 << 64) - 1
 
 

@@ -1,7 +1,9 @@
 """The cyclic 3-way join R(A,B) |><| S(B,C) |><| T(C,A) on the GPU against
 the oracle: |Q|, every row (row ids and columns) in canonical order, windows
 across emit tiles, the empty result, 2^64 overflow, and the calls that have
-no meaning for its cluster summary.  Integer work: exact equality."""
+no meaning for its cluster summary.  Every case runs with each way of
+intersecting the segments (chosen, sorted lists, bitmaps).  Integer work:
+exact equality."""
 import numpy as np
 import pytest
 
@@ -14,12 +16,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=[0, 1, 2], ids=["chosen", "lists", "bitmaps"])
+def ctx(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2206_10435_gb300 import gj
     c = gj.Context(0)
+    c.set_option(gj.GJ_OPT_TRIANGLE_INTERSECT, request.param)
     yield c
     c.close()
 
@@ -108,3 +111,39 @@ def test_tree_only_calls_rejected(ctx):
         run.q.summary_groups(0)
     assert e.value.status == gj.GJ_ERR_INVALID
     run.close()
+
+
+@pytest.mark.parametrize("shift", [-2**31, -17, 2**31 - 64])
+def test_keys_at_the_int32_ends(ctx, shift):
+    # bitmap rows and bits are offsets from the smallest key: keys next to
+    # INT32_MIN / INT32_MAX must not wrap
+    q = G.triangle_query(77, [400, 300, 500], domain=60, s=0.5)
+    for r in q.relations:
+        r.keys = [(k.astype(np.int64) + shift).astype(np.int32) for k in r.keys]
+    assert triangle_parity(ctx, q, windows=[(5, 900)]) > 0
+
+
+def test_c_ranges_of_s_and_t_differ(ctx):
+    # S's c values in [0, 40), T's in [25, 90): only [25, 40) can close the cycle
+    q = G.triangle_query(78, [300, 400, 400], domain=40)
+    T = q.relations[2]
+    T.keys[0] = (T.keys[0] * 65 // 40 + 25).astype(np.int32)
+    assert triangle_parity(ctx, q, windows=[(3, 100)]) > 0
+
+
+def test_c_range_too_wide_for_bitmaps(ctx):
+    # C spans all of int32: bitmaps would take 2^29 bytes per row, so every
+    # mode intersects sorted lists; the result is the same
+    q = G.triangle_query(79, [200, 200, 200], domain=8)
+    S, T = q.relations[1], q.relations[2]
+    S.keys[1] = np.where(S.keys[1] == 0, np.int32(-2**31), S.keys[1]).astype(np.int32)
+    T.keys[0] = np.where(T.keys[0] == 7, np.int32(2**31 - 1), T.keys[0]).astype(np.int32)
+    assert triangle_parity(ctx, q) > 0
+
+
+def test_intersect_option_validated(ctx):
+    from paper_2206_10435_gb300 import gj
+    for bad in (-1, 3):
+        with pytest.raises(gj.GJError) as e:
+            ctx.set_option(gj.GJ_OPT_TRIANGLE_INTERSECT, bad)
+        assert e.value.status == gj.GJ_ERR_INVALID
