@@ -78,6 +78,42 @@ __global__ void k_pack(PackSpec ps, const uint32_t *__restrict__ rows, int64_t n
     }
 }
 
+// keys[i] = packed fields of row rows[i]; pos[i] = i (a position in the
+// order rows[] lists the rows in)
+__global__ void k_pack_pos(PackSpec ps, const uint32_t *__restrict__ rows, int64_t n,
+                           uint64_t *__restrict__ keys, uint32_t *__restrict__ pos) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        const uint32_t r = rows[i];
+        uint64_t k = 0;
+#pragma unroll
+        for (int c = 0; c < MAX_KEYS; c++) {
+            if (c < ps.ncol && ps.shift[c] < 64)
+                k |= (uint64_t)((uint32_t)ps.col[c][r] - (uint32_t)ps.mn[c]) << ps.shift[c];
+        }
+        keys[i] = k;
+        pos[i] = (uint32_t)i;
+    }
+}
+
+// the row ids and the low word in the final order: element i came from
+// position pos[i] of the order the low word was sorted in
+__global__ void k_compose(const uint32_t *__restrict__ pos, const uint32_t *__restrict__ perm0,
+                          const uint64_t *__restrict__ lo0, int64_t n, uint32_t *__restrict__ perm,
+                          uint64_t *__restrict__ lo) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
+        const uint32_t j = pos[i];
+        perm[i] = perm0[j];
+        lo[i] = lo0[j];
+    }
+}
+
+// head[i]: the two-word key (hi, lo) differs from the previous one
+__global__ void k_heads_packed2(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
+                                int64_t n, uint8_t *head) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        head[i] = (i == 0) || hi[i] != hi[i - 1] || lo[i] != lo[i - 1];
+}
+
 // head[i] = i == 0 || key tuple of perm[i] != key tuple of perm[i-1]
 __global__ void k_heads_packed(const uint64_t *__restrict__ keys, int64_t n, uint8_t *head) {
     for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
@@ -110,15 +146,17 @@ __global__ void k_group_compact(ColSet cs, const uint32_t *__restrict__ perm,
     if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
 }
 
-// Where each key column sits in the single packed word of a sorted key:
-// value = ((key >> shift) & (2^bits - 1)) + min.  Columns outside the
-// factor's order (projected away) are read through perm instead.
+// Where each key column sits in the packed words of a sorted key (the low
+// word, or the high one of a two-word key): value = ((word >> shift) &
+// (2^bits - 1)) + min.  Columns outside the factor's order (projected
+// away) are read through perm instead.
 struct UnpackSpec {
     int ncol;
     int col[MAX_KEYS];
     int32_t mn[MAX_KEYS];
     int shift[MAX_KEYS];
     int bits[MAX_KEYS];
+    int hi[MAX_KEYS];
     int nother;
     int other_col[MAX_KEYS];
     const int32_t *other[MAX_KEYS];
@@ -127,6 +165,7 @@ struct UnpackSpec {
 // group starts and key values from the sorted packed keys (no random reads
 // of the key columns)
 __global__ void k_group_compact_packed(UnpackSpec u, const uint64_t *__restrict__ keys,
+                                       const uint64_t *__restrict__ keys_hi,
                                        const uint32_t *__restrict__ perm,
                                        const uint8_t *__restrict__ head,
                                        const uint32_t *__restrict__ gid, int64_t n, int64_t G,
@@ -135,8 +174,9 @@ __global__ void k_group_compact_packed(UnpackSpec u, const uint64_t *__restrict_
         if (!head[i]) continue;
         const uint32_t g = gid[i];
         gstart[g] = (uint32_t)i;
-        const uint64_t k = keys[i];
+        const uint64_t klo = keys[i], khi = keys_hi ? keys_hi[i] : 0ull;
         for (int c = 0; c < u.ncol; c++) {
+            const uint64_t k = u.hi[c] ? khi : klo;
             const uint64_t mask = u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << u.bits[c]) - 1);
             const uint32_t v = (u.shift[c] < 64 ? (uint32_t)((k >> u.shift[c]) & mask) : 0u) + (uint32_t)u.mn[c];
             gkey[(int64_t)u.col[c] * G + g] = (int32_t)v;
@@ -251,7 +291,10 @@ struct FactorBuild {
     Factor *F = nullptr;
     std::vector<int> bits;
     std::vector<std::vector<int>> words;
-    uint64_t *keys = nullptr;
+    uint64_t *keys = nullptr;      // the (low) packed word, in sorted order
+    uint64_t *keys_hi = nullptr;   // a two-word key's high word, in sorted order
+    uint64_t *lo = nullptr;        // two-word key: the low word, moved to the final order
+    uint32_t *pos = nullptr, *perm = nullptr;
     uint8_t *head = nullptr;
     uint32_t *gid = nullptr, *gcount = nullptr;
     int32_t *sorted = nullptr;
@@ -259,6 +302,10 @@ struct FactorBuild {
 
 void fb_free(Ctx &c, FactorBuild &b) {
     dfree(c, b.keys);
+    dfree(c, b.keys_hi);
+    dfree(c, b.lo);
+    dfree(c, b.pos);
+    dfree(c, b.perm);
     dfree(c, b.head);
     dfree(c, b.gid);
     dfree(c, b.gcount);
@@ -299,9 +346,13 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
         if (!cur.empty()) words.push_back(cur);
     }
     GJ_CUDA_TRY(dalloc(c, &b.keys, n));
-    uint64_t *keys = b.keys;
-    bool first = true;
-    for (auto &wcols : words) {   // least significant word first
+    // A two-word key sorts its high word carrying positions in the low
+    // word's sorted order instead of row ids: one gather then brings the row
+    // ids and the low word into the final order, and the groups are found
+    // and unpacked from the two words (no re-read of the key columns).
+    const bool two = words.size() == 2;
+    for (size_t w = 0; w < words.size(); w++) {   // least significant word first
+        const std::vector<int> &wcols = words[w];
         PackSpec ps{};
         ps.ncol = (int)wcols.size();
         int shift = 0;
@@ -312,11 +363,28 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             ps.shift[i] = shift;
             shift += bits[col];
         }
-        k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, first ? nullptr : F.perm, n, keys, F.perm); c.launches++;
-        GJ_CUDA_TRY(cudaGetLastError());
-        GJ_CUDA_TRY(radix_sort_u64_u32(c, keys, F.perm, n, shift));
-        first = false;
+        if (two && w == 1) {
+            GJ_CUDA_TRY(dalloc(c, &b.keys_hi, n));
+            GJ_CUDA_TRY(dalloc(c, &b.pos, n));
+            k_pack_pos<<<grid_for(c, n), FT, 0, c.stream>>>(ps, F.perm, n, b.keys_hi, b.pos); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            GJ_CUDA_TRY(radix_sort_u64_u32(c, b.keys_hi, b.pos, n, shift));
+            GJ_CUDA_TRY(dalloc(c, &b.lo, n));
+            GJ_CUDA_TRY(dalloc(c, &b.perm, n));
+            k_compose<<<grid_for(c, n), FT, 0, c.stream>>>(b.pos, F.perm, b.keys, n, b.perm, b.lo); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            std::swap(F.perm, b.perm);
+            std::swap(b.keys, b.lo);
+            dfree(c, b.perm);
+            dfree(c, b.lo);
+            dfree(c, b.pos);
+        } else {
+            k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, w == 0 ? nullptr : F.perm, n, b.keys, F.perm); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            GJ_CUDA_TRY(radix_sort_u64_u32(c, b.keys, F.perm, n, shift));
+        }
     }
+    uint64_t *keys = b.keys;
     GJ_CUDA_TRY(dalloc(c, &b.head, n));
     GJ_CUDA_TRY(dalloc(c, &b.gid, n));
     GJ_CUDA_TRY(dalloc(c, &b.gcount, 1));
@@ -328,8 +396,10 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
     int32_t *&sorted = b.sorted;
     if (words.size() == 1) {
         k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(keys, n, head); c.launches++;
+    } else if (two) {
+        k_heads_packed2<<<grid_for(c, n), FT, 0, c.stream>>>(b.keys_hi, keys, n, head); c.launches++;
     } else {
-        // the key spans several words: bring the columns into sorted order
+        // the key spans more than two words: bring the columns into sorted order
         // once, then find heads and groups with sequential reads
         GJ_CUDA_TRY(dalloc(c, &sorted, (size_t)R.nk * n));
         k_gather_cols<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, sorted); c.launches++;
@@ -376,16 +446,19 @@ cudaError_t fb_groups(Ctx &c, FactorBuild &b, int64_t G) {
                                                                     F.gstart, F.gkey); c.launches++;
         dfree(c, sorted);
     } else {
-        // one packed word: unpack the key values of every group head
+        // one or two packed words: unpack the key values of every group head
         UnpackSpec u{};
-        int shift = 0;
-        for (int col : words[0]) {   // least significant first, as packed
-            u.col[u.ncol] = col;
-            u.mn[u.ncol] = R.kmin[col];
-            u.shift[u.ncol] = shift;
-            u.bits[u.ncol] = bits[col];
-            shift += bits[col];
-            u.ncol++;
+        for (size_t w = 0; w < words.size(); w++) {
+            int shift = 0;
+            for (int col : words[w]) {   // least significant first, as packed
+                u.col[u.ncol] = col;
+                u.mn[u.ncol] = R.kmin[col];
+                u.shift[u.ncol] = shift;
+                u.bits[u.ncol] = bits[col];
+                u.hi[u.ncol] = (int)w;
+                shift += bits[col];
+                u.ncol++;
+            }
         }
         for (int col = 0; col < R.nk; col++) {
             if (std::find(order.begin(), order.end(), col) != order.end()) continue;
@@ -393,8 +466,8 @@ cudaError_t fb_groups(Ctx &c, FactorBuild &b, int64_t G) {
             u.other[u.nother] = R.key[col];
             u.nother++;
         }
-        k_group_compact_packed<<<grid_for(c, n), FT, 0, c.stream>>>(u, keys, F.perm, head, gid, n, F.G,
-                                                                    F.gstart, F.gkey); c.launches++;
+        k_group_compact_packed<<<grid_for(c, n), FT, 0, c.stream>>>(u, keys, b.keys_hi, F.perm, head, gid, n,
+                                                                    F.G, F.gstart, F.gkey); c.launches++;
     }
     GJ_CUDA_TRY(cudaGetLastError());
     for (int p = 0; p < R.np; p++) {
