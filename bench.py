@@ -370,7 +370,7 @@ def main():
     tpr, tnote = emit_traffic_per_row() if a.workload == "chain5_zipf" and not drop_list(a) else (None, "captured for chain5_zipf (all columns) only")
     rows_per_launch = prof["emit_rows"] / max(prof["emit_launches"], 1)
     traffic = tpr * rows_per_launch if tpr is not None else None
-    roofline = {"bound": "hbm", "kernel": "k_emit<K=5,RPT=4> (desummarise emit)",
+    roofline = {"bound": "hbm", "kernel": f"k_emit<K={len(q.relations)},RPT={a.emit_rpt}> (desummarise emit)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "traffic_note": tnote,
