@@ -19,16 +19,21 @@ namespace gj {
 namespace {
 
 // tile_first[t] = block holding the first row of emit tile t (rows
-// [row0 + t*tile_rows, ...)); written by the blocks themselves, one scatter.
+// [row0 + t*tile_rows, ...)): the last block whose first row is <= that
+// row, by a binary search of the block offsets per tile (a window has far
+// fewer tiles than blocks, and the top levels of the searches stay in
+// cache).
 __global__ void k_tile_first(const uint64_t *__restrict__ A, const uint32_t *B_dev, uint64_t row0,
-                             int64_t n, int64_t tiles, int64_t tile_rows, uint32_t *tile_first) {
+                             int64_t tiles, int64_t tile_rows, uint32_t *tile_first) {
     const int64_t B = *B_dev;
-    for (int64_t b = (int64_t)blockIdx.x * EMIT_DT + threadIdx.x; b < B; b += (int64_t)gridDim.x * EMIT_DT) {
-        uint64_t lo = A[b] > row0 ? A[b] - row0 : 0;
-        uint64_t hi = (b + 1 < B) ? A[b + 1] - row0 : (uint64_t)n;
-        int64_t t0 = (int64_t)((lo + tile_rows - 1) / tile_rows);
-        int64_t t1 = (int64_t)((hi + tile_rows - 1) / tile_rows);
-        for (int64_t t = t0; t < t1 && t < tiles; t++) tile_first[t] = (uint32_t)b;
+    for (int64_t t = (int64_t)blockIdx.x * EMIT_DT + threadIdx.x; t < tiles; t += (int64_t)gridDim.x * EMIT_DT) {
+        const uint64_t row = row0 + (uint64_t)(t * tile_rows);
+        int64_t lo = 0, hi = B;   // first block whose first row is > row
+        while (lo < hi) {
+            const int64_t m = (lo + hi) >> 1;
+            if (A[m] <= row) lo = m + 1; else hi = m;
+        }
+        tile_first[t] = (uint32_t)(lo > 0 ? lo - 1 : 0);
     }
 }
 
@@ -278,9 +283,8 @@ cudaError_t launch_k(Ctx &c, const Emit4Spec &s, const uint32_t *B_dev, uint64_t
     uint32_t *tile_first = nullptr;
     if (!pre) {
         GJ_CUDA_TRY(dalloc(c, &tile_first, tiles + 1));
-        // at most one block per row of the window
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, EMIT_DT), (int64_t)c.num_sms * 16));
-        k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, n, tiles, TILE, tile_first); c.launches++;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(tiles, EMIT_DT), (int64_t)c.num_sms * 16));
+        k_tile_first<<<(unsigned)grid, EMIT_DT, 0, c.stream>>>(s.A, B_dev, row0, tiles, TILE, tile_first); c.launches++;
     }
     if (c.prof) cudaEventRecord(c.event(), c.stream);
     k_emit<K, RPT><<<(unsigned)tiles, EMIT_DT, 0, c.stream>>>(s, pre ? pre : tile_first, tiles, B_dev, row0, n); c.launches++;
