@@ -35,6 +35,9 @@ struct SatAddU64 {
 template <class T>
 __device__ __forceinline__ T ld_volatile(const T *p) { return *(const volatile T *)p; }
 
+template <int PAD>
+__device__ __forceinline__ int padded(int e) { return e + e / PAD; }
+
 // Tile status of the unsegmented scans: a flag (ST_A: the tile's aggregate
 // is published, ST_P: its inclusive prefix is) and the value, written and
 // read as one word so that a reader never pairs a flag with another
@@ -127,7 +130,12 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
        T *seg_total, const uint32_t *__restrict__ seg_id, uint32_t *err,
        const uint32_t *n_dev) {
     constexpr int TILE = SCAN_THREADS * ITEMS;
-    __shared__ T s_val[TILE];
+    // one padding element per 128 bytes: the coalesced phases (a warp on 32
+    // consecutive elements) and the per-thread phases (a thread on ITEMS
+    // consecutive elements, 64 bytes apart between threads) are then both
+    // free of bank conflicts
+    constexpr int PAD = 128 / (int)sizeof(T);
+    __shared__ T s_val[TILE + TILE / PAD];
     __shared__ uint8_t s_head[SEG ? TILE : 1];
     __shared__ T s_warp_v[SCAN_THREADS / 32];
     __shared__ uint32_t s_warp_h[SCAN_THREADS / 32];
@@ -163,7 +171,7 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
                 v = in ? in[idx] : T(flags_as_values[idx] != 0);
                 if (SEG) h = heads[idx] != 0;
             }
-            s_val[i * SCAN_THREADS + tid] = v;
+            s_val[padded<PAD>(i * SCAN_THREADS + tid)] = v;
             if (SEG) s_head[i * SCAN_THREADS + tid] = h;
         }
         __syncthreads();
@@ -175,7 +183,7 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
         uint32_t any_head = 0;
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
-            x[i] = s_val[tid * ITEMS + i];
+            x[i] = s_val[padded<PAD>(tid * ITEMS + i)];
             hx[i] = SEG ? s_head[tid * ITEMS + i] : 0;
             if (SEG && hx[i]) { run = x[i]; any_head = 1; }
             else run = op(run, x[i]);
@@ -260,7 +268,7 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             if (SEG && hx[i]) r = T(0);
-            s_val[tid * ITEMS + i] = r;
+            s_val[padded<PAD>(tid * ITEMS + i)] = r;
             r = op(r, x[i]);
             if (SEG && seg_total) {
                 int64_t idx = base + tid * ITEMS + i;
@@ -274,7 +282,7 @@ k_scan(const T *__restrict__ in, const uint8_t *__restrict__ flags_as_values,
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             int64_t idx = base + i * SCAN_THREADS + tid;
-            if (idx < n) out[idx] = s_val[i * SCAN_THREADS + tid];
+            if (idx < n) out[idx] = s_val[padded<PAD>(i * SCAN_THREADS + tid)];
         }
         if (!PERSIST) return;
         __syncthreads();
