@@ -124,7 +124,7 @@ __device__ __forceinline__ void emit_store_col(const T (&v)[RPT], T *dst, int64_
 }
 
 template <int K, int RPT>
-__global__ void __launch_bounds__(EMIT_DT, (RPT == 8 ? 2 : RPT == 4 ? (K <= 5 ? 4 : 3) : (K <= 5 ? 6 : 4)))
+__global__ void __launch_bounds__(EMIT_DT, (RPT == 8 ? 2 : RPT == 4 ? (K <= 3 ? 5 : K <= 5 ? 4 : 3) : (K <= 5 ? 6 : 4)))
 k_emit(Emit4Spec e, const uint32_t *__restrict__ tile_first, int64_t tiles, const uint32_t *B_dev,
        uint64_t row0, int64_t n) {
     constexpr int TILE = EMIT_DT * RPT;
