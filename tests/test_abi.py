@@ -35,3 +35,19 @@ def test_create_fails_cleanly_without_gpu():
     h = ctypes.c_void_p()
     st = gj.lib().gj_create(ctypes.byref(h), 0, None)
     assert st == gj.GJ_ERR_CUDA and not h.value
+
+
+def test_binding_constants_match_the_header():
+    # every GJ_* value the Python binding mirrors (status codes, relation
+    # flags, options) is the one include/gj.h defines
+    import re
+    text = open(gj.HEADER).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"^\s*#define\s+(GJ_[A-Z0-9_]+)\s+(\d+)u?\s*(?:/\*.*)?$", text, re.M)}
+    defs.update({m.group(1): int(m.group(2)) for m in
+                 re.finditer(r"^\s*(GJ_[A-Z0-9_]+)\s*=\s*(\d+)\s*,?", text, re.M)})
+    mirrored = {n: getattr(gj, n) for n in dir(gj) if n.startswith("GJ_") and isinstance(getattr(gj, n), int)}
+    assert {"GJ_OK", "GJ_ERR_CAPACITY", "GJ_REL_HOST", "GJ_OPT_TRIANGLE_INTERSECT"} <= set(mirrored)
+    for n, v in mirrored.items():
+        assert n in defs, n
+        assert defs[n] == v, (n, defs[n], v)
