@@ -200,12 +200,10 @@ constexpr size_t RS_SMEM = (size_t)RS_TILE * 8 + (size_t)RS_TILE * 4 +
 cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits) {
     if (n <= 1 || bits <= 0) return cudaSuccess;
     if (n > 0x7fffffffLL || bits > 64) return cudaErrorInvalidValue;
-    static bool attr_set = false;
-    if (!attr_set) {
-        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RS_SMEM));
-        attr_set = true;
-    }
+    // the limit belongs to the current device: set it on every call (cheap,
+    // and right for every device and thread)
+    GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)RS_SMEM));
     const int passes = (bits + 7) / 8;
     const int64_t tiles = ceil_div(n, RS_TILE);
     uint64_t *k2 = nullptr;
