@@ -29,8 +29,8 @@ struct Emit4Spec {
 // Emits result rows [row0, row0 + n) from the block list A with the emit
 // kernel for K = k relations (k <= 8).  B_dev: number of blocks, in device
 // memory.  tile_first: the block holding the first row of every tile of
-// EMIT_DT * c.emit_rpt rows, or NULL to have it computed here (a
-// tile-to-block scatter over the blocks).
+// EMIT_DT * c.emit_rpt rows, or NULL to have it computed here (a binary
+// search of the block offsets per tile).
 cudaError_t launch_emit(Ctx &c, int k, const Emit4Spec &s, const uint32_t *B_dev, uint64_t row0,
                         int64_t n, const uint32_t *tile_first = nullptr);
 
