@@ -236,7 +236,10 @@ def run_reference(a, rank, world):
            "warmup": a.warmup, "ms_per_step": 1000 * secs / a.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": workload_name(a), "inputs": "larger than L2"},
+           "config": {"workload": workload_name(a),
+                      "input_bytes": int(sum(sum(x.nbytes for x in R.keys + R.payloads) for R in q.relations)),
+                      "l2": "inputs larger than L2 (no flush)",
+                      "parallelism": "one host process (the oracle, one core)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"root cut to first {a.cpu_sample_rows // 4} rows per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
