@@ -284,6 +284,38 @@ def test_cyclic_triangle_all_equal_keys_gives_product():
     assert O.count(q).total == 7 * 5 * 3
 
 
+@pytest.mark.parametrize("seed,s", [(0, 0.0), (1, 0.9), (2, 1.5), (3, 0.4)])
+def test_cyclic_triangle_size_is_the_trace_of_the_count_matrices(seed, s):
+    # |R(A,B) join S(B,C) join T(C,A)| = sum over (a,b,c) of
+    # n_R(a,b) n_S(b,c) n_T(c,a) = trace(M_R M_S M_T), with M the tables'
+    # pair-count matrices: a library matrix product, independent of the
+    # oracle's hash joins
+    d = 12 + seed
+    q = G.triangle_query(9100 + seed, [300, 250, 400], domain=d, s=s)
+    M = []
+    for R in q.relations:
+        m = np.zeros((d, d), np.int64)
+        np.add.at(m, (R.keys[0].astype(np.int64), R.keys[1].astype(np.int64)), 1)
+        M.append(m)
+    # R is (A,B), S is (B,C), T is (C,A)
+    assert O.count(q).total == int(np.trace(M[0] @ M[1] @ M[2]))
+
+
+def test_cyclic_triangle_complete_tripartite_closed_form():
+    # every pair present m times in each table: |Q| = |A| |B| |C| m_R m_S m_T
+    na, nb, nc, mr, ms, mt = 3, 4, 2, 2, 3, 1
+    def full(xs, ys, m, attrs, name):
+        x = np.repeat(np.array([u for u in xs for _ in ys], np.int32), m)
+        y = np.repeat(np.array([v for _ in xs for v in ys], np.int32), m)
+        return G.Relation(name, attrs, [x, y])
+    A, B, C = range(-1, na - 1), range(10, 10 + nb), range(5, 5 + nc)
+    q = G.Query("k_abc", [full(A, B, mr, [0, 1], "R"), full(B, C, ms, [1, 2], "S"),
+                          full(C, A, mt, [2, 0], "T")], {0: "A", 1: "B", 2: "C"})
+    assert O.count(q).total == na * nb * nc * mr * ms * mt
+    j = O.join(q)
+    assert j.rowids.shape[0] == na * nb * nc * mr * ms * mt
+
+
 def test_other_cyclic_queries_are_rejected():
     # a 4-cycle, and a triangle one of whose relations holds a third key:
     # neither is a join tree nor the supported 3-cycle
