@@ -284,6 +284,33 @@ def test_cyclic_triangle_all_equal_keys_gives_product():
     assert O.count(q).total == 7 * 5 * 3
 
 
+@pytest.mark.parametrize("k,seed,s", [(2, 0, 0.0), (3, 1, 0.8), (4, 2, 1.3), (5, 3, 1.1), (5, 4, 0.0)])
+def test_chain_counts_are_products_of_the_count_matrices(k, seed, s):
+    # For R_i(K_{i-1}, K_i), i = 1..k, with M_i the pair-count matrix of R_i:
+    # |Q| = 1' M_1 ... M_k 1, and a row (x, y) of R_i is in
+    # (1' M_1 ... M_{i-1})[x] * (M_{i+1} ... M_k 1)[y] result tuples: the
+    # upward and downward messages of the counting pass, by library matrix
+    # products (Eq. 6-10's sum-product on a chain), independent of the oracle
+    d = [7 + (seed + j) % 5 for j in range(k + 1)]
+    q = G.chain_query(f"chain{k}", [40 + 17 * i for i in range(k)], d, [s] * (k + 1), None, 9300 + seed)
+    M = []
+    for i, R in enumerate(q.relations):
+        m = np.zeros((d[i], d[i + 1]), np.int64)
+        np.add.at(m, (R.keys[0].astype(np.int64), R.keys[1].astype(np.int64)), 1)
+        M.append(m)
+    left = [np.ones(d[0], np.int64)]
+    for i in range(k):
+        left.append(left[-1] @ M[i])
+    right = [np.ones(d[k], np.int64)]
+    for i in reversed(range(k)):
+        right.insert(0, M[i] @ right[0])
+    c = O.count(q, rows=True)
+    assert c.total == int(left[k].sum()) == int(right[0].sum())
+    for i, R in enumerate(q.relations):
+        want = left[i][R.keys[0]] * right[i + 1][R.keys[1]]
+        assert np.array_equal(c.mult[i].astype(np.int64), want), i
+
+
 @pytest.mark.parametrize("seed,s", [(0, 0.0), (1, 0.9), (2, 1.5), (3, 0.4)])
 def test_cyclic_triangle_size_is_the_trace_of_the_count_matrices(seed, s):
     # |R(A,B) join S(B,C) join T(C,A)| = sum over (a,b,c) of
