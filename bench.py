@@ -4,7 +4,9 @@ One step = the whole path over one synthetic instance of the workload:
 factor construction of every relation, the summary (upward and downward
 sum-product passes, offsets), and desummarisation of every result row into
 device columns, chunk by chunk.  Inputs are resident in HBM before the timed
-region (they are larger than L2, so no flush is needed between steps).
+region.  Those of the default workload are larger than L2, so nothing is
+flushed between steps; when a workload's inputs fit in L2, a buffer twice the
+L2 is written before every timed step and that time is taken out.
 
 Default workload: 5-table chain R_i(K_{i-1}, K_i), 10^7 rows per table,
 int32 keys Zipf(s=1.1) over a domain of 10^6 (independently permuted per
@@ -238,7 +240,7 @@ def run_reference(a, rank, world):
            "impl": "reference",
            "config": {"workload": workload_name(a),
                       "input_bytes": int(sum(sum(x.nbytes for x in R.keys + R.payloads) for R in q.relations)),
-                      "l2": "inputs larger than L2 (no flush)",
+                      "l2": "not applicable: the oracle runs on the host",
                       "parallelism": "one host process (the oracle, one core)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"root cut to first {a.cpu_sample_rows // 4} rows per step"},
@@ -299,6 +301,11 @@ def main():
         rels.append(([torch.from_numpy(k).to(dev) for k in R.keys],
                      [torch.from_numpy(p).to(dev) for p in R.payloads], R.attrs))
     in_bytes = sum(sum(t.numel() * t.element_size() for t in ks + ps) for ks, ps, _ in rels)
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (128 << 20))
+    flush_buf = torch.empty(2 * l2_bytes, dtype=torch.uint8, device=dev) if in_bytes <= l2_bytes else None
+    l2_note = ("inputs larger than L2 (no flush)" if flush_buf is None else
+               f"inputs ({in_bytes / 1e6:.1f} MB) fit in L2 ({l2_bytes / 1e6:.0f} MB): a "
+               f"{2 * l2_bytes / 1e6:.0f} MB buffer is written before every timed step, outside the timed time")
     stream = torch.cuda.Stream(dev)
     ctx = gj.Context(local, stream)
     ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, a.emit_rpt)
@@ -345,15 +352,23 @@ def main():
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
-        evs = []
-        for _ in range(a.steps):
+        evs, flush_evs = [], []
+        for k in range(a.steps):
+            if flush_buf is not None:
+                # inputs that fit in L2: evict them before every timed step
+                # (writing a buffer twice the L2); this time is taken out
+                fe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                fe[0].record(stream)
+                flush_buf.fill_(k & 0xff)
+                fe[1].record(stream)
+                flush_evs.append(fe)
             total, ev = step(record=True)
             evs.append(ev)
         t_end.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop()
         prof = ctx.profile(False)
-        elapsed_ms = t_start.elapsed_time(t_end)
+        elapsed_ms = t_start.elapsed_time(t_end) - sum(f[0].elapsed_time(f[1]) for f in flush_evs)
         for ev in evs:
             phase["build_ms"] += ev[0].elapsed_time(ev[1]) / a.steps
             phase["summary_ms"] += ev[1].elapsed_time(ev[2]) / a.steps
@@ -420,7 +435,7 @@ def main():
                "dtype": "int64", "data": "synthetic",
                "config": {"workload": workload_name(a), "join_size": total,
                           "result_row_bytes": row_bytes, "input_bytes": in_bytes,
-                          "l2": "inputs larger than L2 (no flush)",
+                          "l2": l2_note,
                           "parallelism": f"{world} independent instances (one per GPU)"},
                "summary_build_ms": phase["build_ms"] + phase["summary_ms"],
                "phases_ms": phase,
