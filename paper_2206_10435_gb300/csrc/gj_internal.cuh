@@ -50,13 +50,13 @@ struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     // stream-ordered pool owned by the context; it keeps freed memory for
-    // reuse instead of returning it to the driver at every synchronisation
+    // reuse instead of returning it to the CUDA driver at every synchronisation
     cudaMemPool_t pool = nullptr;
     uint32_t *err = nullptr;          // device error word
     uint64_t *pinned = nullptr;       // small pinned host buffer for readbacks
     int num_sms = 0;
     uint64_t launches = 0;            // kernels launched (profiling)
-    int emit_rpt = 4;                 // result rows per thread of the emit kernel (2 or 4)
+    int emit_rpt = 4;                 // result rows per thread of the emit kernel (2, 4 or 8)
     int tri_mode = 0;                 // triangle intersection: 0 chooses, 1 sorted lists, 2 bitmaps
     // device-time profile of the emit kernel (CUDA events on the stream)
     bool prof = false;
