@@ -51,3 +51,18 @@ def test_binding_constants_match_the_header():
     for n, v in mirrored.items():
         assert n in defs, n
         assert defs[n] == v, (n, defs[n], v)
+
+
+def test_every_entry_point_rejects_null_handles():
+    # the boundary's error behaviour: NULL handles and pointers give
+    # GJ_ERR_INVALID (destroy calls are no-ops), never a crash; no GPU needed
+    L = ctypes.CDLL(build.LIB)
+    void_fns = {"gj_destroy", "gj_query_destroy", "gj_batch_destroy", "gj_server_destroy"}
+    for name in gj.header_functions():
+        if name in ("gj_status_str", "gj_version", "gj_last_error"):
+            continue
+        f = getattr(L, name)
+        f.restype = None if name in void_fns else ctypes.c_int
+        r = f(*([None] * 12))
+        if name not in void_fns:
+            assert r == gj.GJ_ERR_INVALID, (name, r)
