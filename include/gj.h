@@ -128,6 +128,8 @@ gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
  * used only while they take at most 512 MiB, else lists).  The triples and
  * their order are the same either way.  Takes effect at the next
  * gj_summarize.
+ * Unknown options and values outside these ranges return GJ_ERR_INVALID
+ * and change nothing; a NULL ctx returns GJ_ERR_INVALID.
  */
 #define GJ_OPT_EMIT_ROWS_PER_THREAD 1
 #define GJ_OPT_TRIANGLE_INTERSECT 2
