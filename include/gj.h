@@ -383,7 +383,9 @@ void gj_server_destroy(gj_server *server);
  * n_rows + 1 entries; n_groups + 1 are written), gkey_dev (capacity
  * n_keys * n_rows; column c of group g at gkey[c*n_groups + g]) and
  * *n_groups.  key_cols is a host array of n_keys device pointers.  Work is
- * enqueued on `cuda_stream` on `device`; the call synchronises that stream.
+ * enqueued on `cuda_stream` on `device`.  Every call waits for that stream
+ * before it returns: it reads the key ranges, the group count and the
+ * device error word back into host memory.
  *
  * All scratch lives in one fixed device array inside the library (about
  * 6.7 MB, held on every device that loads the library until the process

@@ -119,6 +119,20 @@ cudaError_t scan_u64_sat(Ctx &c, const uint64_t *in, const uint8_t *heads, uint6
 // keys/vals are sorted in place (ping-pong through internal buffers).
 cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits);
 
+// Tile sizes of the radix sort and of the 32-bit scans: callers that lay out
+// the sort's status words or a scan's lookback state themselves (the
+// allocation-free factor build) size them from these.
+constexpr int RADIX_SORT_TILE = 256 * 16;   // keys per onesweep tile
+constexpr int RADIX_SORT_BINS = 256;        // digit values per pass
+constexpr int RADIX_SORT_MAX_PASSES = 8;
+constexpr int SCAN_U32_TILE = 256 * 16;     // elements per 32-bit scan tile
+
+// Bytes of lookback state scan_u32_in needs for n elements.
+constexpr size_t scan_u32_state_bytes_for(int64_t n) {
+    return 16 + ((((size_t)((n > 0 ? n : 1) + SCAN_U32_TILE - 1) / SCAN_U32_TILE) * 4 + 15) & ~(size_t)15) +
+           2 * (size_t)(((n > 0 ? n : 1) + SCAN_U32_TILE - 1) / SCAN_U32_TILE) * sizeof(uint32_t);
+}
+
 // ------------------------------------------------------------------ helpers
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 

@@ -30,7 +30,8 @@ size_t scan_u32_state_bytes(int64_t n);
 namespace {
 
 constexpr int64_t NA_ROWS = GJ_NOALLOC_MAX_ROWS;
-constexpr int64_t NA_TILES = (NA_ROWS + 4095) / 4096;   // sort and scan tiles of 4096
+// onesweep tiles of the sort (one status word per tile and digit value)
+constexpr int64_t NA_TILES = (NA_ROWS + RADIX_SORT_TILE - 1) / RADIX_SORT_TILE;
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t OFF_ERR = 0;
@@ -38,14 +39,17 @@ constexpr size_t OFF_KEYS = 256;
 constexpr size_t OFF_K2 = OFF_KEYS + a256(8 * NA_ROWS);
 constexpr size_t OFF_V2 = OFF_K2 + a256(8 * NA_ROWS);
 constexpr size_t OFF_HIST = OFF_V2 + a256(4 * NA_ROWS);
-constexpr size_t OFF_STATUS = OFF_HIST + a256(4 * (8 * 256 + 8));
-constexpr size_t OFF_HEAD = OFF_STATUS + a256(8 * 256 * NA_TILES);
+constexpr size_t HIST_WORDS = RADIX_SORT_MAX_PASSES * RADIX_SORT_BINS + RADIX_SORT_MAX_PASSES;
+constexpr size_t OFF_STATUS = OFF_HIST + a256(4 * HIST_WORDS);
+constexpr size_t OFF_HEAD = OFF_STATUS + a256(8 * RADIX_SORT_BINS * NA_TILES);
 constexpr size_t OFF_GID = OFF_HEAD + a256(NA_ROWS);
 constexpr size_t OFF_GCOUNT = OFF_GID + a256(4 * NA_ROWS);
 constexpr size_t OFF_MM = OFF_GCOUNT + 256;
 constexpr size_t OFF_SCAN = OFF_MM + 256;
-constexpr size_t SCAN_BYTES = 16 + ((4 * NA_TILES + 15) & ~15) + 8 * NA_TILES;
+constexpr size_t SCAN_BYTES = scan_u32_state_bytes_for(NA_ROWS);
 constexpr size_t SCRATCH_BYTES = OFF_SCAN + a256(SCAN_BYTES);
+static_assert(2 * 4 * MAX_KEYS <= 256, "the key ranges fit their 256-byte slot");
+static_assert(SCRATCH_BYTES < (8u << 20), "the fixed scratch stays under 8 MB");
 
 static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 

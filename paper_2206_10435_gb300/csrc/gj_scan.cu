@@ -362,11 +362,9 @@ namespace gj {
 
 // scan_u32 with the lookback state in caller memory (no device allocation):
 // state must hold scan_u32_state_bytes(n) bytes.
-size_t scan_u32_state_bytes(int64_t n) {
-    int64_t tiles = ceil_div(n > 0 ? n : 1, SCAN_THREADS * 16);
-    size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
-    return 16 + flag_bytes + 2 * (size_t)tiles * sizeof(uint32_t);
-}
+static_assert(SCAN_THREADS * 16 == SCAN_U32_TILE, "the 32-bit scan tile is exported through gj_internal.cuh");
+
+size_t scan_u32_state_bytes(int64_t n) { return scan_u32_state_bytes_for(n); }
 
 cudaError_t scan_u32_in(Ctx &c, const uint32_t *in, const uint8_t *flags, uint32_t *out,
                         int64_t n, uint32_t *total_dev, void *state_mem, size_t state_bytes) {

@@ -29,6 +29,9 @@ constexpr int RS_ITEMS = 16;
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;       // 4096 keys
 constexpr int RS_RADIX = 256;
 constexpr int RS_MAX_PASSES = 8;
+static_assert(RS_TILE == RADIX_SORT_TILE && RS_RADIX == RADIX_SORT_BINS &&
+                  RS_MAX_PASSES == RADIX_SORT_MAX_PASSES,
+              "the sort's tile layout is exported through gj_internal.cuh");
 constexpr uint64_t ST_AGG = 1ull << 62, ST_PREFIX = 2ull << 62, ST_MASK = (1ull << 62) - 1;
 
 __global__ void __launch_bounds__(RS_THREADS)

@@ -60,6 +60,21 @@ def test_noalloc_factor_equals_allocating_entry_point():
             assert torch.equal(perm, ref_perm)
             assert torch.equal(gstart[:G + 1], ref_gstart)
             assert torch.equal(gkey[:len(cols) * G].view(len(cols), G), ref_gkey)
+    # an empty relation (no groups, gstart = [0]) and a one-row relation (one
+    # group) skip the sort; both still match the allocating path
+    for n_small in (0, 1):
+        small = [torch.from_numpy(rng.integers(-5, 5, n_small, dtype=np.int32)).cuda() for _ in range(2)]
+        sid = ctx.load_relation(small, [0, 1])
+        ref_perm, ref_gstart, ref_gkey = ctx.factor_export(sid, n_small, 2, [1, 0])
+        for _ in range(2):
+            st, G, perm, gstart, gkey = _noalloc(L, gj, small, [1, 0], n_small)
+            torch.cuda.synchronize()
+            assert st == gj.GJ_OK, L.gj_status_str(st)
+            assert G == n_small == ref_gstart.numel() - 1
+            assert torch.equal(perm, ref_perm[:n_small])
+            assert torch.equal(gstart[:G + 1], ref_gstart)
+            assert torch.equal(gkey[:2 * G].view(2, G), ref_gkey.view(2, G))
+        ctx.release_relation(sid)
     # sizes beyond the fixed scratch are refused before any work
     n, cols = rels[0]
     st, G, *_ = _noalloc(L, gj, cols, [0, 1, 2], n_max + 1)
