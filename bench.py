@@ -306,7 +306,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
-    q = make_query(a, rank)
+    from paper_2206_10435_gb300 import partition as P
+    # every rank builds the same instance (factors and summary replicated);
+    # each desummarises its own equal, contiguous share of the result rows
+    q = make_query(a, 0)
     rels = []
     for R in q.relations:
         rels.append(([torch.from_numpy(k).to(dev) for k in R.keys],
@@ -334,10 +337,11 @@ def main():
         total = qq.summarize()                    # upward + downward passes
         if record:
             ev[2].record(stream)
+        lo, hi = P.row_range(total, rank, world)
         if out_bufs is None:
-            out_bufs = qq.alloc_columns(min(CH, total))
-        for r0 in range(0, total, CH):
-            qq.desummarize(r0, CH, out=out_bufs)
+            out_bufs = qq.alloc_columns(max(1, min(CH, hi - lo)))
+        for r0, n in P.windows(lo, hi, CH):
+            qq.desummarize(r0, n, out=out_bufs)
         if record:
             ev[3].record(stream)
         qq.close()
@@ -380,7 +384,8 @@ def main():
             phase["build_ms"] += ev[0].elapsed_time(ev[1]) / a.steps
             phase["summary_ms"] += ev[1].elapsed_time(ev[2]) / a.steps
             phase["desum_ms"] += ev[2].elapsed_time(ev[3]) / a.steps
-    rows_local = total * a.steps
+    lo, hi = P.row_range(total, rank, world)
+    rows_local = (hi - lo) * a.steps
     t_max, rows_all = reduce_over_ranks(dist, elapsed_ms, rows_local, dev)
     value = rows_all / (t_max / 1000.0)
 
@@ -388,7 +393,7 @@ def main():
     # from pinned memory, the whole path, D2H of every result chunk
     e2e = None
     if not a.no_e2e:
-        e2e = run_e2e(a, q, ctx, stream, dev, total, dist)
+        e2e = run_e2e(a, q, ctx, stream, dev, total, dist, rank, world)
 
     peak, peak_kind = measured_peaks()
     achieved = (prof["emit_bytes"] / (prof["emit_ms"] * 1e6)) if prof["emit_ms"] else None
@@ -438,12 +443,14 @@ def main():
         row_bytes = int(prof["emit_bytes"] // max(prof["emit_rows"], 1))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                "dtype": "int64", "data": "synthetic",
                "config": {"workload": workload_name(a), "join_size": total,
                           "result_row_bytes": row_bytes, "input_bytes": in_bytes,
                           "l2": l2_note,
-                          "parallelism": f"{world} independent instances (one per GPU)"},
+                          "parallelism": (f"{world} rank(s), one per GPU: factors and summary "
+                                          "built on every rank, the result rows split into "
+                                          "equal contiguous ranges, one per rank")},
                "summary_build_ms": phase["build_ms"] + phase["summary_ms"],
                "phases_ms": phase,
                "phase_rooflines": phase_rooflines,
@@ -523,8 +530,21 @@ def run_batch(a, rank, world, local):
         warm_ms = e0.elapsed_time(e1) / a.steps
         batched = [int(x) for x in b.totals.cpu().numpy().view(np.uint64)]
     same = batched == [int(x) for x in plain_totals]
+    # the global query list is the ranks' sets in rank order: totals of all
+    # of them, gathered in query order (the slowest rank's time counts)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2206_10435_gb300 import partition as P
+    all_totals = P.gather_in_order(dist, np.array(batched, dtype=np.uint64), a.queries * world,
+                                   rank, world, dev)
+    warm_ms = P.max_over_ranks(dist, warm_ms, dev)
+    plain_s = P.max_over_ranks(dist, plain_s, dev)
+    cold_s = P.max_over_ranks(dist, cold_s, dev)
+    same = P.max_over_ranks(dist, 0.0 if same else 1.0, dev) == 0.0
     out = {"metric": "queries summarised/s (batched, one CUDA-graph launch)",
-           "value": a.queries / (warm_ms / 1000.0), "unit": "queries/s", "n_gpus": world,
+           "value": a.queries * world / (warm_ms / 1000.0), "unit": "queries/s", "n_gpus": world,
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": warm_ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
            "data": "synthetic",
@@ -533,18 +553,23 @@ def run_batch(a, rank, world, local):
                                    "uniform in [0,1.5], int32 keys; totals per query"),
                       "rows": n_rows, "relations": b.n_relations, "levels": b.levels,
                       "key_bits": b.key_bits, "generation_s": gen_s,
-                      "l2": "inputs larger than L2 (no flush)"},
-           "plain_qps": a.queries / plain_s, "plain_s": plain_s,
-           "batched_cold_qps": a.queries / cold_s, "batched_cold_s": cold_s,
+                      "l2": "inputs larger than L2 (no flush)",
+                      "parallelism": (f"{world} rank(s): each summarises its own {a.queries} "
+                                      "queries (one block of the global query list); totals "
+                                      "gathered in query order")},
+           "plain_qps": a.queries * world / plain_s, "plain_s": plain_s,
+           "batched_cold_qps": a.queries * world / cold_s, "batched_cold_s": cold_s,
            "speedup_warm_vs_plain": plain_s / (warm_ms / 1000.0),
            "speedup_cold_vs_plain": plain_s / cold_s,
            "identical_totals": same,
-           "overflowed_queries": sum(1 for x in batched if x == gj.SAT),
+           "overflowed_queries": int(np.sum(all_totals == np.uint64(gj.SAT))),
            "autotune": tuned, "gpu_launches": int(prof["launches"]), "clocks": clk}
     if rank == 0:
         print(json.dumps(out), flush=True)
     b.close()
     ctx.close()
+    if dist:
+        dist.destroy_process_group()
     if not same:
         sys.exit(1)
 
@@ -766,9 +791,9 @@ def run_sensitivity(a, rank, world, local):
     ctx.close()
 
 
-def run_e2e(a, q, ctx, stream, dev, total, dist):
+def run_e2e(a, q, ctx, stream, dev, total, dist, rank=0, world=1):
     import torch
-    from paper_2206_10435_gb300 import gj
+    from paper_2206_10435_gb300 import gj, partition as P
     host = []
     h2d = 0
     for R in q.relations:
@@ -795,8 +820,9 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
             ids = [ctx.load_relation(ks, attrs, ps, flags=gj.GJ_REL_HOST) for ks, ps, attrs in host]
             qq = ctx.query(ids, drop_attrs=drop_list(a))
             tot = qq.summarize()
-            for r0 in range(0, tot, CH):
-                qq.desummarize(r0, CH, out=hbuf)
+            lo, hi = P.row_range(tot, rank, world)
+            for r0, n in P.windows(lo, hi, CH):
+                qq.desummarize(r0, n, out=hbuf)
             stream.synchronize()
             qq.close()
             for i in ids:
@@ -811,8 +837,9 @@ def run_e2e(a, q, ctx, stream, dev, total, dist):
         for _ in range(a.e2e_steps):
             tot = one()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-    d2h = tot * row_bytes
+        dt = P.max_over_ranks(dist, time.perf_counter() - t0, dev)
+    lo, hi = P.row_range(tot, rank, world)
+    d2h = (hi - lo) * row_bytes
     return {"value": tot * a.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": a.e2e_steps,
             "chunk_rows": CH, "note": "relations H2D from pinned host memory; every result chunk "

@@ -5,20 +5,25 @@
 // key tuple and cutting the sorted order into groups:
 //
 //   1. per key column, min and max (one read of every column);
-//   2. each column becomes an unsigned field of ceil(log2(max-min+1)) bits;
-//      fields are packed into 64-bit words, most significant column first,
-//      and the words are sorted least significant first with the stable
-//      radix sort (one word suffices unless the fields exceed 64 bits);
-//   3. group heads are the rows whose packed key differs from the previous
-//      row's; an exclusive scan numbers the groups;
-//   4. each group records its first position and its key values; payload
-//      columns are gathered into group order.
+//   2. each column becomes an unsigned field of ceil(log2(max-min+1)) bits,
+//      packed into 64-bit words, most significant column first.  When the
+//      key and the row id fit one word together, the row id rides in the low
+//      bits and a keys-only LSD radix sort orders the key bits (a stable
+//      sort of rows taken in row order keeps equal keys in row order);
+//      otherwise (word, row id) pairs are sorted, word by word.  The first
+//      pass builds the words from the key columns itself;
+//   3. one group scan over the sorted words marks the rows whose key differs
+//      from the previous row's, numbers these group heads (a single-pass
+//      scan with decoupled lookback) and writes the row order, every group's
+//      first position and key values, and the payload columns gathered
+//      into group order.
 //
 // Sorted order is also the order the desummariser walks: groups sharing a
 // separator value are contiguous (the separator columns lead the order) and
 // inside a group rows keep increasing row id.
 #include <algorithm>
 
+#include "gj_lookback.cuh"
 #include "gj_state.cuh"
 
 namespace gj {
@@ -107,13 +112,6 @@ __global__ void k_compose(const uint32_t *__restrict__ pos, const uint32_t *__re
     }
 }
 
-// head[i]: the two-word key (hi, lo) differs from the previous one
-__global__ void k_heads_packed2(const uint64_t *__restrict__ hi, const uint64_t *__restrict__ lo,
-                                int64_t n, uint8_t *head) {
-    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
-        head[i] = (i == 0) || hi[i] != hi[i - 1] || lo[i] != lo[i - 1];
-}
-
 // head[i] = i == 0 || key tuple of perm[i] != key tuple of perm[i-1]
 __global__ void k_heads_packed(const uint64_t *__restrict__ keys, int64_t n, uint8_t *head) {
     for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
@@ -161,33 +159,6 @@ struct UnpackSpec {
     int other_col[MAX_KEYS];
     const int32_t *other[MAX_KEYS];
 };
-
-// group starts and key values from the sorted packed keys (no random reads
-// of the key columns)
-__global__ void k_group_compact_packed(UnpackSpec u, const uint64_t *__restrict__ keys,
-                                       const uint64_t *__restrict__ keys_hi,
-                                       const uint32_t *__restrict__ perm,
-                                       const uint8_t *__restrict__ head,
-                                       const uint32_t *__restrict__ gid, int64_t n, int64_t G,
-                                       uint32_t *gstart, int32_t *gkey) {
-    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
-        if (!head[i]) continue;
-        const uint32_t g = gid[i];
-        gstart[g] = (uint32_t)i;
-        const uint64_t klo = keys[i], khi = keys_hi ? keys_hi[i] : 0ull;
-        for (int c = 0; c < u.ncol; c++) {
-            const uint64_t k = u.hi[c] ? khi : klo;
-            const uint64_t mask = u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << u.bits[c]) - 1);
-            const uint32_t v = (u.shift[c] < 64 ? (uint32_t)((k >> u.shift[c]) & mask) : 0u) + (uint32_t)u.mn[c];
-            gkey[(int64_t)u.col[c] * G + g] = (int32_t)v;
-        }
-        if (u.nother) {
-            const uint32_t r = perm[i];
-            for (int c = 0; c < u.nother; c++) gkey[(int64_t)u.other_col[c] * G + g] = u.other[c][r];
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) gstart[G] = (uint32_t)n;
-}
 
 // sorted[c*n + i] = col_c[perm[i]]: the key columns in sorted order, one
 // random read per column and row (used when the key spans several words)
@@ -282,6 +253,189 @@ void factor_free(Ctx &c, Factor &F) {
 
 namespace {
 
+// ------------------------------------------------------------ group scan
+// One pass over the sorted words: a row starts a group when its key differs
+// from the previous row's; the groups are numbered by a single-pass scan
+// with decoupled lookback, and the same pass writes the row order, every
+// group's first position and key values, and the payloads in group order.
+//   MODE 0  one word per row, the row id in its low row_bits bits
+//   MODE 1  one word per row (the key), row order in perm_in
+//   MODE 2  two words per row (hi, lo), row order in perm_in
+constexpr int GS_THREADS = 256;
+constexpr int GS_ITEMS = 16;
+constexpr int GS_TILE = GS_THREADS * GS_ITEMS;
+
+struct GroupScanSpec {
+    const uint64_t *lo;           // sorted words (the low word of two)
+    const uint64_t *hi;           // MODE 2: the high word
+    const uint32_t *perm_in;      // MODE 1, 2
+    uint32_t *perm_out;           // MODE 0: the row order taken from the words
+    int row_bits;
+    UnpackSpec u;                 // where each key column sits in the words
+    int np;
+    const void *pay_in[MAX_PAYLOADS];
+    void *pay_out[MAX_PAYLOADS];
+    int pw[MAX_PAYLOADS];
+    uint32_t *gstart;             // [G+1]
+    int32_t *gkey;                // column c of group g at c * gkey_stride + g
+    int64_t gkey_stride;
+    uint32_t *gcount;             // G
+    unsigned long long *status;   // lookback state, one word per tile
+    uint32_t *counter;            // tile counter
+    uint32_t *err;
+};
+
+// shared-memory slot of word q (q = 0 is the previous tile's last word): one
+// pad word per 16, so that threads reading 16 consecutive words each are
+// free of bank conflicts
+__device__ __forceinline__ int gs_slot(int q) { return q + (q >> 4); }
+constexpr int GS_SLOTS = GS_TILE + 1 + (GS_TILE + 1) / 16 + 1;
+
+template <int MODE>
+__global__ void __launch_bounds__(GS_THREADS)
+k_group_scan(GroupScanSpec s, int64_t n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_lo = (uint64_t *)smem;
+    uint64_t *s_hi = s_lo + GS_SLOTS;          // MODE 2 only
+    __shared__ uint32_t s_wsum[GS_THREADS / 32];
+    __shared__ uint32_t s_tile, s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(s.counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * GS_TILE;
+    if (base >= n) return;
+    const int tile_n = (int)min((int64_t)GS_TILE, n - base);
+    {
+        // the tile's words, 16 loads in flight per thread
+        uint64_t a[GS_ITEMS];
+#pragma unroll
+        for (int i = 0; i < GS_ITEMS; i++) {
+            const int64_t idx = base + i * GS_THREADS + tid;
+            a[i] = idx < n ? __ldg((const unsigned long long *)s.lo + idx) : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < GS_ITEMS; i++) s_lo[gs_slot(i * GS_THREADS + tid + 1)] = a[i];
+        if (MODE == 2) {
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++) {
+                const int64_t idx = base + i * GS_THREADS + tid;
+                a[i] = idx < n ? __ldg((const unsigned long long *)s.hi + idx) : 0ull;
+            }
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++) s_hi[gs_slot(i * GS_THREADS + tid + 1)] = a[i];
+        }
+    }
+    if (tid == 0) {
+        s_lo[0] = base > 0 ? s.lo[base - 1] : 0ull;
+        if (MODE == 2) s_hi[0] = base > 0 ? s.hi[base - 1] : 0ull;
+    }
+    __syncthreads();
+    // heads among the thread's 16 consecutive rows
+    uint32_t hmask = 0;
+#pragma unroll
+    for (int i = 0; i < GS_ITEMS; i++) {
+        const int e = tid * GS_ITEMS + i;
+        if (e < tile_n) {
+            const uint64_t a = s_lo[gs_slot(e + 1)], b = s_lo[gs_slot(e)];
+            bool h;
+            if (MODE == 0) h = (a >> s.row_bits) != (b >> s.row_bits);
+            else if (MODE == 1) h = a != b;
+            else h = a != b || s_hi[gs_slot(e + 1)] != s_hi[gs_slot(e)];
+            if (h || base + e == 0) hmask |= 1u << i;
+        }
+    }
+    // tile-wide exclusive count of heads, then the carry-in by lookback
+    const uint32_t cnt = __popc(hmask);
+    uint32_t x = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_wsum[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, agg = 0;
+#pragma unroll
+    for (int w = 0; w < GS_THREADS / 32; w++) {
+        const uint32_t v = s_wsum[w];
+        if (w < warp) before += v;
+        agg += v;
+    }
+    const uint32_t excl = before + x - cnt;
+    if (warp == GS_THREADS / 32 - 1) {
+        const uint32_t carry = warp_lookback<uint32_t, AddU32>(s.status, tile, agg, lane, s.err);
+        if (lane == 0) {
+            s_carry = carry;
+            if (base + GS_TILE >= n) {   // the last tile: the group count
+                *s.gcount = carry + agg;
+                s.gstart[carry + agg] = (uint32_t)n;
+            }
+        }
+    }
+    __syncthreads();
+    // group starts and keys
+    uint32_t g = s_carry + excl;
+    const uint64_t rmask = s.row_bits ? ((1ull << s.row_bits) - 1) : 0ull;
+    while (hmask) {
+        const int i = __ffs(hmask) - 1;
+        hmask &= hmask - 1;
+        const int e = tid * GS_ITEMS + i;
+        const int64_t idx = base + e;
+        s.gstart[g] = (uint32_t)idx;
+        const uint64_t klo = s_lo[gs_slot(e + 1)], khi = MODE == 2 ? s_hi[gs_slot(e + 1)] : 0ull;
+        for (int c = 0; c < s.u.ncol; c++) {
+            const uint64_t k = s.u.hi[c] ? khi : klo;
+            const uint64_t mask = s.u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << s.u.bits[c]) - 1);
+            const uint32_t v = (s.u.shift[c] < 64 ? (uint32_t)((k >> s.u.shift[c]) & mask) : 0u) + (uint32_t)s.u.mn[c];
+            s.gkey[(int64_t)s.u.col[c] * s.gkey_stride + g] = (int32_t)v;
+        }
+        if (s.u.nother) {
+            const uint32_t r = MODE == 0 ? (uint32_t)(klo & rmask) : s.perm_in[idx];
+            for (int c = 0; c < s.u.nother; c++)
+                s.gkey[(int64_t)s.u.other_col[c] * s.gkey_stride + g] = s.u.other[c][r];
+        }
+        g++;
+    }
+    // row order and payloads in group order, coalesced; each thread issues
+    // its 16 gathers of a payload column together
+    uint32_t r[GS_ITEMS];
+#pragma unroll
+    for (int i = 0; i < GS_ITEMS; i++) {
+        const int e = i * GS_THREADS + tid;
+        if (MODE == 0) r[i] = (uint32_t)(s_lo[gs_slot(e + 1)] & rmask);
+        else r[i] = e < tile_n ? __ldg(s.perm_in + base + e) : 0u;
+    }
+    if (MODE == 0) {
+#pragma unroll
+        for (int i = 0; i < GS_ITEMS; i++) {
+            const int e = i * GS_THREADS + tid;
+            if (e < tile_n) s.perm_out[base + e] = r[i];
+        }
+    }
+    for (int p = 0; p < s.np; p++) {
+        if (s.pw[p] == 8) {
+            const unsigned long long *src = (const unsigned long long *)s.pay_in[p];
+            unsigned long long *dst = (unsigned long long *)s.pay_out[p];
+            unsigned long long v[GS_ITEMS];
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++) v[i] = i * GS_THREADS + tid < tile_n ? __ldg(src + r[i]) : 0ull;
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++)
+                if (i * GS_THREADS + tid < tile_n) dst[base + i * GS_THREADS + tid] = v[i];
+        } else {
+            const unsigned int *src = (const unsigned int *)s.pay_in[p];
+            unsigned int *dst = (unsigned int *)s.pay_out[p];
+            unsigned int v[GS_ITEMS];
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++) v[i] = i * GS_THREADS + tid < tile_n ? __ldg(src + r[i]) : 0u;
+#pragma unroll
+            for (int i = 0; i < GS_ITEMS; i++)
+                if (i * GS_THREADS + tid < tile_n) dst[base + i * GS_THREADS + tid] = v[i];
+        }
+    }
+}
+
 // One factor build in two stages, so that the builds of several relations
 // share their host synchronisations: the key ranges (for the packed field
 // widths) before the sort, and the group counts (for the group arrays)
@@ -291,42 +445,108 @@ struct FactorBuild {
     Factor *F = nullptr;
     std::vector<int> bits;
     std::vector<std::vector<int>> words;
-    uint64_t *keys = nullptr;      // the (low) packed word, in sorted order
-    uint64_t *keys_hi = nullptr;   // a two-word key's high word, in sorted order
-    uint64_t *lo = nullptr;        // two-word key: the low word, moved to the final order
-    uint32_t *pos = nullptr, *perm = nullptr;
+    // fused path (keys of at most two words): the group scan wrote gstart,
+    // the keys at stride n, the payloads and the count
+    bool fused = false;
+    uint32_t *gstart = nullptr;    // [n+1]
+    int32_t *gkey_n = nullptr;     // [nk*n]
+    uint32_t *gcount = nullptr;
+    // keys of more than two words
     uint8_t *head = nullptr;
-    uint32_t *gid = nullptr, *gcount = nullptr;
+    uint32_t *gid = nullptr;
     int32_t *sorted = nullptr;
 };
 
 void fb_free(Ctx &c, FactorBuild &b) {
-    dfree(c, b.keys);
-    dfree(c, b.keys_hi);
-    dfree(c, b.lo);
-    dfree(c, b.pos);
-    dfree(c, b.perm);
+    dfree(c, b.gstart);
+    dfree(c, b.gkey_n);
+    dfree(c, b.gcount);
     dfree(c, b.head);
     dfree(c, b.gid);
-    dfree(c, b.gcount);
     dfree(c, b.sorted);
 }
 
-// stage 1 (key ranges known): rows sorted by the key tuple, group heads
-// marked and numbered; the group count lands in b.gcount
+// the key fields of `order` for the group scan: column cols[i] at bit
+// shift[i] of word hi[i]
+UnpackSpec unpack_spec(const Relation &R, const std::vector<int> &order,
+                       const std::vector<std::vector<int>> &words, const std::vector<int> &bits,
+                       int row_bits) {
+    UnpackSpec u{};
+    for (size_t w = 0; w < words.size(); w++) {
+        int shift = w == 0 ? row_bits : 0;
+        for (int col : words[w]) {   // least significant first, as packed
+            u.col[u.ncol] = col;
+            u.mn[u.ncol] = R.kmin[col];
+            u.shift[u.ncol] = shift;
+            u.bits[u.ncol] = bits[col];
+            u.hi[u.ncol] = (int)w;
+            shift += bits[col];
+            u.ncol++;
+        }
+    }
+    for (int col = 0; col < R.nk; col++) {
+        if (std::find(order.begin(), order.end(), col) != order.end()) continue;
+        u.other_col[u.nother] = col;
+        u.other[u.nother] = R.key[col];
+        u.nother++;
+    }
+    return u;
+}
+
+PackSrc pack_src(const Relation &R, const std::vector<int> &wcols, const std::vector<int> &bits,
+                 int row_bits) {
+    PackSrc ps{};
+    ps.ncol = (int)wcols.size();
+    ps.row_bits = row_bits;
+    int shift = row_bits;
+    for (int i = 0; i < ps.ncol; i++) {   // wcols[0] is the least significant
+        const int col = wcols[i];
+        ps.col[i] = R.key[col];
+        ps.mn[i] = R.kmin[col];
+        ps.shift[i] = shift;
+        shift += bits[col];
+    }
+    return ps;
+}
+
+template <int MODE>
+cudaError_t launch_group_scan(Ctx &c, GroupScanSpec &gs, int64_t n) {
+    const int64_t tiles = ceil_div(n, GS_TILE);
+    unsigned long long *state = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &state, tiles + 2));
+    GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 8 * (tiles + 2), c.stream));
+    gs.counter = (uint32_t *)state;
+    gs.status = state + 2;
+    gs.err = c.err;
+    const size_t smem = (size_t)GS_SLOTS * 8 * (MODE == 2 ? 2 : 1);
+    GJ_CUDA_TRY(cudaFuncSetAttribute(k_group_scan<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_group_scan<MODE><<<(unsigned)tiles, GS_THREADS, smem, c.stream>>>(gs, n); c.launches++;
+    cudaError_t e = cudaGetLastError();
+    dfree(c, state);
+    return e;
+}
+
+// stage 1 (key ranges known): rows sorted by the key tuple; keys of one or
+// two words go straight on to the group scan (the group count lands in
+// b.gcount), longer keys mark and number their group heads
 cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
     Relation &R = *b.R;
     Factor &F = *b.F;
     const std::vector<int> &order = F.order;
     F.n = R.n;
     const int64_t n = R.n;
-    GJ_CUDA_TRY(dalloc(c, &F.perm, n));
-    if (n == 0) return cudaSuccess;
+    if (n == 0) {
+        GJ_CUDA_TRY(dalloc(c, &F.perm, 1));
+        return cudaSuccess;
+    }
     // field widths, least significant column last in `order`
     std::vector<int> &bits = b.bits;
     bits.assign(R.nk, 0);
     for (int i = 0; i < R.nk; i++)
         bits[i] = bits_of((uint32_t)((int64_t)R.kmax[i] - (int64_t)R.kmin[i]));
+    int kbits = 0;
+    for (int col : order) kbits += bits[col];
+    const int row_bits = bits_of((uint32_t)(n - 1));
     // cut the order into words of <= 64 bits, starting from the least
     // significant column
     std::vector<std::vector<int>> &words = b.words;
@@ -345,12 +565,113 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
         }
         if (!cur.empty()) words.push_back(cur);
     }
-    GJ_CUDA_TRY(dalloc(c, &b.keys, n));
-    // A two-word key sorts its high word carrying positions in the low
-    // word's sorted order instead of row ids: one gather then brings the row
-    // ids and the low word into the final order, and the groups are found
-    // and unpacked from the two words (no re-read of the key columns).
-    const bool two = words.size() == 2;
+    if (words.size() <= 2) {
+        // the fused path: sort, then one group scan
+        b.fused = true;
+        GroupScanSpec gs{};
+        GJ_CUDA_TRY(dalloc(c, &b.gstart, n + 1));
+        GJ_CUDA_TRY(dalloc(c, &b.gkey_n, (size_t)R.nk * n));
+        GJ_CUDA_TRY(dalloc(c, &b.gcount, 1));
+        for (int p = 0; p < R.np; p++) {
+            void *d = nullptr;
+            GJ_CUDA_TRY(dalloc_bytes(c, &d, (size_t)R.pw[p] * n));
+            F.pay.push_back(d);
+            gs.pay_in[p] = R.pay[p];
+            gs.pay_out[p] = d;
+            gs.pw[p] = R.pw[p];
+        }
+        gs.np = R.np;
+        gs.gstart = b.gstart;
+        gs.gkey = b.gkey_n;
+        gs.gkey_stride = n;
+        gs.gcount = b.gcount;
+        uint64_t *k1 = nullptr, *k2 = nullptr, *kres = nullptr;
+        GJ_CUDA_TRY(dalloc(c, &k1, n));
+        GJ_CUDA_TRY(dalloc(c, &k2, n));
+        if (words.size() == 1 && kbits + row_bits <= 64) {
+            // MODE 0: the row id rides under the key; a keys-only sort of the
+            // key bits
+            PackSrc ps = pack_src(R, words[0], bits, row_bits);
+            GJ_CUDA_TRY(radix_sort_words(c, &ps, k1, k2, nullptr, nullptr, n, row_bits, kbits, &kres, nullptr));
+            GJ_CUDA_TRY(dalloc(c, &F.perm, n));
+            gs.lo = kres;
+            gs.perm_out = F.perm;
+            gs.row_bits = row_bits;
+            gs.u = unpack_spec(R, order, words, bits, row_bits);
+            GJ_CUDA_TRY(launch_group_scan<0>(c, gs, n));
+        } else if (words.size() == 1) {
+            // MODE 1: (key, row id) pairs
+            uint32_t *v1 = nullptr, *v2 = nullptr, *vres = nullptr;
+            GJ_CUDA_TRY(dalloc(c, &v1, n));
+            GJ_CUDA_TRY(dalloc(c, &v2, n));
+            PackSrc ps = pack_src(R, words[0], bits, 0);
+            GJ_CUDA_TRY(radix_sort_words(c, &ps, k1, k2, v1, v2, n, 0, kbits, &kres, &vres));
+            // the sorted row ids become the factor's row order
+            F.perm = vres;
+            if (vres == v1) dfree(c, v2); else dfree(c, v1);
+            gs.lo = kres;
+            gs.perm_in = F.perm;
+            gs.u = unpack_spec(R, order, words, bits, 0);
+            GJ_CUDA_TRY(launch_group_scan<1>(c, gs, n));
+        } else {
+            // MODE 2: the low word sorts with row ids; the high word sorts
+            // carrying positions in the low word's order, and one gather then
+            // brings the row ids and the low word into the final order
+            uint32_t *v1 = nullptr, *v2 = nullptr, *perm0 = nullptr;
+            GJ_CUDA_TRY(dalloc(c, &v1, n));
+            GJ_CUDA_TRY(dalloc(c, &v2, n));
+            PackSrc ps = pack_src(R, words[0], bits, 0);
+            int lo_bits = 0;
+            for (int col : words[0]) lo_bits += bits[col];
+            uint64_t *lo_sorted = nullptr;
+            GJ_CUDA_TRY(radix_sort_words(c, &ps, k1, k2, v1, v2, n, 0, lo_bits, &lo_sorted, &perm0));
+            uint32_t *vfree = perm0 == v1 ? v2 : v1;   // free buffer of n values
+            uint64_t *kfree = lo_sorted == k1 ? k2 : k1;
+            PackSpec ph{};
+            ph.ncol = (int)words[1].size();
+            int shift = 0;
+            for (int i = 0; i < ph.ncol; i++) {
+                const int col = words[1][i];
+                ph.col[i] = R.key[col];
+                ph.mn[i] = R.kmin[col];
+                ph.shift[i] = shift;
+                shift += bits[col];
+            }
+            uint64_t *h1 = nullptr, *hres = nullptr;
+            uint32_t *pos2 = nullptr, *pres = nullptr;
+            GJ_CUDA_TRY(dalloc(c, &h1, n));
+            GJ_CUDA_TRY(dalloc(c, &pos2, n));
+            k_pack_pos<<<grid_for(c, n), FT, 0, c.stream>>>(ph, perm0, n, kfree, vfree); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            GJ_CUDA_TRY(radix_sort_words(c, nullptr, kfree, h1, vfree, pos2, n, 0, shift, &hres, &pres));
+            uint64_t *lo_final = hres == kfree ? h1 : kfree;   // the buffer hres does not hold
+            uint32_t *perm = pres == vfree ? pos2 : vfree;
+            k_compose<<<grid_for(c, n), FT, 0, c.stream>>>(pres, perm0, lo_sorted, n, perm, lo_final); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            F.perm = perm;
+            // free everything but perm, hres and lo_final
+            for (uint32_t *v : {v1, v2, pos2})
+                if (v != perm) dfree(c, v);
+            for (uint64_t *k : {k1, k2, h1})
+                if (k != hres && k != lo_final) dfree(c, k);
+            k1 = hres;
+            k2 = lo_final;
+            gs.lo = lo_final;
+            gs.hi = hres;
+            gs.perm_in = F.perm;
+            gs.u = unpack_spec(R, order, words, bits, 0);
+            GJ_CUDA_TRY(launch_group_scan<2>(c, gs, n));
+        }
+        dfree(c, k1);
+        dfree(c, k2);
+        return cudaSuccess;
+    }
+    // keys of three or more words: (word, row id) sorts word by word, then
+    // the key columns are brought into sorted order once and the groups are
+    // found with sequential reads
+    GJ_CUDA_TRY(dalloc(c, &F.perm, n));
+    uint64_t *keys = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &keys, n));
     for (size_t w = 0; w < words.size(); w++) {   // least significant word first
         const std::vector<int> &wcols = words[w];
         PackSpec ps{};
@@ -363,62 +684,33 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             ps.shift[i] = shift;
             shift += bits[col];
         }
-        if (two && w == 1) {
-            GJ_CUDA_TRY(dalloc(c, &b.keys_hi, n));
-            GJ_CUDA_TRY(dalloc(c, &b.pos, n));
-            k_pack_pos<<<grid_for(c, n), FT, 0, c.stream>>>(ps, F.perm, n, b.keys_hi, b.pos); c.launches++;
-            GJ_CUDA_TRY(cudaGetLastError());
-            GJ_CUDA_TRY(radix_sort_u64_u32(c, b.keys_hi, b.pos, n, shift));
-            GJ_CUDA_TRY(dalloc(c, &b.lo, n));
-            GJ_CUDA_TRY(dalloc(c, &b.perm, n));
-            k_compose<<<grid_for(c, n), FT, 0, c.stream>>>(b.pos, F.perm, b.keys, n, b.perm, b.lo); c.launches++;
-            GJ_CUDA_TRY(cudaGetLastError());
-            std::swap(F.perm, b.perm);
-            std::swap(b.keys, b.lo);
-            dfree(c, b.perm);
-            dfree(c, b.lo);
-            dfree(c, b.pos);
-        } else {
-            k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, w == 0 ? nullptr : F.perm, n, b.keys, F.perm); c.launches++;
-            GJ_CUDA_TRY(cudaGetLastError());
-            GJ_CUDA_TRY(radix_sort_u64_u32(c, b.keys, F.perm, n, shift));
-        }
+        k_pack<<<grid_for(c, n), FT, 0, c.stream>>>(ps, w == 0 ? nullptr : F.perm, n, keys, F.perm); c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        GJ_CUDA_TRY(radix_sort_u64_u32(c, keys, F.perm, n, shift));
     }
-    uint64_t *keys = b.keys;
+    dfree(c, keys);
     GJ_CUDA_TRY(dalloc(c, &b.head, n));
     GJ_CUDA_TRY(dalloc(c, &b.gid, n));
     GJ_CUDA_TRY(dalloc(c, &b.gcount, 1));
-    uint8_t *head = b.head;
-    uint32_t *gid = b.gid, *gcount = b.gcount;
     ColSet all{};
     all.ncol = R.nk;
     for (int i = 0; i < R.nk; i++) all.col[i] = R.key[i];
-    int32_t *&sorted = b.sorted;
-    if (words.size() == 1) {
-        k_heads_packed<<<grid_for(c, n), FT, 0, c.stream>>>(keys, n, head); c.launches++;
-    } else if (two) {
-        k_heads_packed2<<<grid_for(c, n), FT, 0, c.stream>>>(b.keys_hi, keys, n, head); c.launches++;
-    } else {
-        // the key spans more than two words: bring the columns into sorted order
-        // once, then find heads and groups with sequential reads
-        GJ_CUDA_TRY(dalloc(c, &sorted, (size_t)R.nk * n));
-        k_gather_cols<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, sorted); c.launches++;
-        ColIdx by{};
-        by.n = (int)order.size();
-        for (int i = 0; i < by.n; i++) by.idx[i] = order[i];
-        k_heads_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, by, n, head); c.launches++;
-    }
+    GJ_CUDA_TRY(dalloc(c, &b.sorted, (size_t)R.nk * n));
+    k_gather_cols<<<grid_for(c, n), FT, 0, c.stream>>>(all, F.perm, n, b.sorted); c.launches++;
+    ColIdx by{};
+    by.n = (int)order.size();
+    for (int i = 0; i < by.n; i++) by.idx[i] = order[i];
+    k_heads_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(b.sorted, by, n, b.head); c.launches++;
     GJ_CUDA_TRY(cudaGetLastError());
-    GJ_CUDA_TRY(scan_u32(c, nullptr, head, gid, n, gcount));
+    GJ_CUDA_TRY(scan_u32(c, nullptr, b.head, b.gid, n, b.gcount));
     return cudaSuccess;
 }
 
-// stage 2 (group count G known): group starts and keys, payloads in group
-// order; frees the stage's temporaries
+// stage 2 (group count G known): the group arrays at their final size,
+// payloads in group order; frees the stage's temporaries
 cudaError_t fb_groups(Ctx &c, FactorBuild &b, int64_t G) {
     Relation &R = *b.R;
     Factor &F = *b.F;
-    const std::vector<int> &order = F.order;
     const int64_t n = R.n;
     if (n == 0) {
         F.G = 0;
@@ -432,43 +724,23 @@ cudaError_t fb_groups(Ctx &c, FactorBuild &b, int64_t G) {
         }
         return cudaSuccess;
     }
-    const std::vector<int> &bits = b.bits;
-    const std::vector<std::vector<int>> &words = b.words;
-    uint64_t *keys = b.keys;
-    uint8_t *head = b.head;
-    uint32_t *gid = b.gid;
-    int32_t *&sorted = b.sorted;
     F.G = G;
+    if (b.fused) {
+        // group starts stay in their n + 1 slots; the keys move from stride
+        // n to stride G
+        F.gstart = b.gstart;
+        b.gstart = nullptr;
+        GJ_CUDA_TRY(dalloc(c, &F.gkey, (size_t)R.nk * G));
+        if (G > 0)
+            GJ_CUDA_TRY(cudaMemcpy2DAsync(F.gkey, sizeof(int32_t) * G, b.gkey_n, sizeof(int32_t) * n,
+                                          sizeof(int32_t) * G, R.nk, cudaMemcpyDeviceToDevice, c.stream));
+        fb_free(c, b);
+        return cudaSuccess;
+    }
     GJ_CUDA_TRY(dalloc(c, &F.gstart, F.G + 1));
     GJ_CUDA_TRY(dalloc(c, &F.gkey, (size_t)R.nk * F.G));
-    if (sorted) {
-        k_group_compact_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(sorted, R.nk, head, gid, n, F.G,
-                                                                    F.gstart, F.gkey); c.launches++;
-        dfree(c, sorted);
-    } else {
-        // one or two packed words: unpack the key values of every group head
-        UnpackSpec u{};
-        for (size_t w = 0; w < words.size(); w++) {
-            int shift = 0;
-            for (int col : words[w]) {   // least significant first, as packed
-                u.col[u.ncol] = col;
-                u.mn[u.ncol] = R.kmin[col];
-                u.shift[u.ncol] = shift;
-                u.bits[u.ncol] = bits[col];
-                u.hi[u.ncol] = (int)w;
-                shift += bits[col];
-                u.ncol++;
-            }
-        }
-        for (int col = 0; col < R.nk; col++) {
-            if (std::find(order.begin(), order.end(), col) != order.end()) continue;
-            u.other_col[u.nother] = col;
-            u.other[u.nother] = R.key[col];
-            u.nother++;
-        }
-        k_group_compact_packed<<<grid_for(c, n), FT, 0, c.stream>>>(u, keys, b.keys_hi, F.perm, head, gid, n,
-                                                                    F.G, F.gstart, F.gkey); c.launches++;
-    }
+    k_group_compact_sorted<<<grid_for(c, n), FT, 0, c.stream>>>(b.sorted, R.nk, b.head, b.gid, n, F.G,
+                                                                F.gstart, F.gkey); c.launches++;
     GJ_CUDA_TRY(cudaGetLastError());
     for (int p = 0; p < R.np; p++) {
         void *d = nullptr;

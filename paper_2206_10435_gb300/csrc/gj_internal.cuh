@@ -115,6 +115,38 @@ cudaError_t scan_u64_sat(Ctx &c, const uint64_t *in, const uint8_t *heads, uint6
                          int64_t n, uint64_t *total_dev, uint64_t *seg_total,
                          const uint32_t *seg_id);
 
+// Key columns packed into one 64-bit word: field c is (col[c][i] - mn[c])
+// at bit shift[c] (a field at shift >= 64 has no bits and is left out);
+// with row_bits > 0 the row id i fills the low row_bits bits, under the key.
+constexpr int PACK_MAX_COLS = 8;
+struct PackSrc {
+    int ncol;
+    const int32_t *col[PACK_MAX_COLS];
+    int32_t mn[PACK_MAX_COLS];
+    int shift[PACK_MAX_COLS];
+    int row_bits;
+};
+
+__device__ __forceinline__ uint64_t pack_word(const PackSrc &ps, int64_t i) {
+    uint64_t k = ps.row_bits ? (uint64_t)i : 0ull;
+#pragma unroll
+    for (int c = 0; c < PACK_MAX_COLS; c++)
+        if (c < ps.ncol && ps.shift[c] < 64)
+            k |= (uint64_t)((uint32_t)__ldg(ps.col[c] + i) - (uint32_t)ps.mn[c]) << ps.shift[c];
+    return k;
+}
+
+// Stable LSD radix sort of 64-bit words on bits [lo_bit, lo_bit + bits),
+// 8 bits per pass.  The words are `pack` applied to rows 0..n-1 when pack is
+// non-NULL (the words are then built by the first pass and never read from
+// memory; `keys` is only a buffer), else keys[0..n).  With vals (non-NULL)
+// each word carries a 32-bit value: the row id when packing, else vals[i].
+// The passes ping-pong between keys/alt (and vals/valt); *kres and *vres
+// receive the buffers holding the sorted result.  Buffers hold n entries.
+cudaError_t radix_sort_words(Ctx &c, const PackSrc *pack, uint64_t *keys, uint64_t *alt,
+                             uint32_t *vals, uint32_t *valt, int64_t n, int lo_bit, int bits,
+                             uint64_t **kres, uint32_t **vres);
+
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).
 // keys/vals are sorted in place (ping-pong through internal buffers).
 cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n, int bits);

@@ -33,16 +33,26 @@ static_assert(RS_TILE == RADIX_SORT_TILE && RS_RADIX == RADIX_SORT_BINS &&
                   RS_MAX_PASSES == RADIX_SORT_MAX_PASSES,
               "the sort's tile layout is exported through gj_internal.cuh");
 constexpr uint64_t ST_AGG = 1ull << 62, ST_PREFIX = 2ull << 62, ST_MASK = (1ull << 62) - 1;
+// predecessors whose status a tile reads per round of its lookback
+#ifndef RS_LOOKBACK
+#define RS_LOOKBACK 4
+#endif
+// resident CTAs per SM the keys-only kernel is compiled for
+#ifndef RS_KEYS_CTAS
+#define RS_KEYS_CTAS 4
+#endif
 
+template <bool PACK>
 __global__ void __launch_bounds__(RS_THREADS)
-k_digit_hist(const uint64_t *__restrict__ keys, int64_t n, int passes, uint32_t *hist) {
+k_digit_hist(const uint64_t *__restrict__ keys, PackSrc ps, int64_t n, int lo_bit, int passes,
+             uint32_t *hist) {
     __shared__ uint32_t sh[RS_MAX_PASSES][RS_RADIX];
     for (int i = threadIdx.x; i < RS_MAX_PASSES * RS_RADIX; i += RS_THREADS) (&sh[0][0])[i] = 0;
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * RS_THREADS) {
-        uint64_t k = keys[i];
-        for (int p = 0; p < passes; p++) atomicAdd(&sh[p][(k >> (8 * p)) & 0xff], 1u);
+        const uint64_t k = PACK ? pack_word(ps, i) : keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&sh[p][(k >> (lo_bit + 8 * p)) & 0xff], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_RADIX; i += RS_THREADS) {
@@ -67,16 +77,28 @@ __global__ void __launch_bounds__(RS_RADIX) k_hist_to_base(uint32_t *hist) {
     h[d] = s[d] - h[d];
 }
 
-template <bool VALS>
-__global__ void __launch_bounds__(RS_THREADS, 3)
-k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *q) {
+    return *(const volatile unsigned long long *)q;
+}
+
+// keys[i] = pack(i), vals[i] = i: a packed sort with nothing to order
+__global__ void k_pack_words(PackSrc ps, int64_t n, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * RS_THREADS) {
+        keys[i] = pack_word(ps, i);
+        if (vals) vals[i] = (uint32_t)i;
+    }
+}
+
+template <bool VALS, bool PACK>
+__global__ void __launch_bounds__(RS_THREADS, VALS ? 3 : RS_KEYS_CTAS)
+k_onesweep_t(const uint64_t *__restrict__ kin, PackSrc ps, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
              const uint32_t *__restrict__ bucket_base, uint32_t *tile_counter,
              unsigned long long *status, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_keys = (uint64_t *)smem;                              // RS_TILE
-    uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);                // RS_TILE
-    uint32_t *s_whist = s_vals + RS_TILE;                             // RS_WARPS*RS_RADIX
+    uint32_t *s_vals = (uint32_t *)(s_keys + RS_TILE);                // RS_TILE (VALS only)
+    uint32_t *s_whist = s_vals + (VALS ? RS_TILE : 0);                // RS_WARPS*RS_RADIX
     uint32_t *s_tile_off = s_whist + RS_WARPS * RS_RADIX;             // RS_RADIX
     uint32_t *s_glob = s_tile_off + RS_RADIX;                         // RS_RADIX
     uint32_t *s_misc = s_glob + RS_RADIX;                             // 8
@@ -92,11 +114,42 @@ k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     uint32_t v[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
     const int64_t wbase = base + warp * (RS_ITEMS * 32);
+    if (PACK) {
+        // pass 0 of a packed sort builds the tile's words from the key
+        // columns, staged in shared memory (the value is then the row id, the
+        // input position); per column, the thread's 16 loads are issued
+        // together
+        uint64_t acc[RS_ITEMS];
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; i++) {
+            const int64_t idx = base + i * RS_THREADS + tid;
+            acc[i] = (ps.row_bits && idx < n) ? (uint64_t)idx : 0ull;
+        }
+        for (int c = 0; c < ps.ncol; c++) {
+            if (ps.shift[c] >= 64) continue;
+            const int32_t *col = ps.col[c];
+            const uint32_t mn = (uint32_t)ps.mn[c];
+            const int sh = ps.shift[c];
+            uint32_t x[RS_ITEMS];
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; i++) {
+                const int64_t idx = base + i * RS_THREADS + tid;
+                x[i] = idx < n ? (uint32_t)__ldg(col + idx) : mn;
+            }
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; i++) acc[i] |= (uint64_t)(x[i] - mn) << sh;
+        }
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; i++) s_keys[i * RS_THREADS + tid] = acc[i];
+        __syncthreads();
+    }
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         int64_t idx = wbase + i * 32 + lane;
-        if (idx < n) { k[i] = kin[idx]; v[i] = VALS ? vin[idx] : 0u; }
-        else { k[i] = 0; v[i] = 0; }
+        if (idx < n) {
+            k[i] = PACK ? s_keys[idx - base] : kin[idx];
+            v[i] = VALS ? (PACK ? (uint32_t)idx : vin[idx]) : 0u;
+        } else { k[i] = 0; v[i] = 0; }
     }
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t *wh = s_whist + warp * RS_RADIX;
@@ -129,22 +182,36 @@ k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     }
     // publish the tile's count of digit d, then look back for its prefix
     unsigned long long *st = status + (size_t)tile * RS_RADIX;
+    atomicExch(&st[d], (unsigned long long)((tile == 0 ? ST_PREFIX : ST_AGG) | cnt));
+    // look back RS_LOOKBACK predecessors per round (their
+    // status words are read together, then folded nearest first; one that
+    // has published nothing yet is polled, bounded, before the fold goes on)
     if (tile == 0) {
-        atomicExch(&st[d], (unsigned long long)(ST_PREFIX | cnt));
         s_glob[d] = bucket_base[d];
     } else {
-        atomicExch(&st[d], (unsigned long long)(ST_AGG | cnt));
         uint64_t excl = 0;
         int64_t p = (int64_t)tile - 1;
-        while (p >= 0) {
-            unsigned long long s;
-            uint32_t spins = 0;
-            while (((s = *(volatile unsigned long long *)&status[(size_t)p * RS_RADIX + d]) >> 62) == 0) {
-                if (++spins > SPIN_LIMIT) { raise_err(err, ERRF_TIMEOUT); s = ST_PREFIX; break; }
+        bool done = false;
+        while (!done && p >= 0) {
+            unsigned long long sv[RS_LOOKBACK];
+#pragma unroll
+            for (int j = 0; j < RS_LOOKBACK; j++)
+                sv[j] = p - j >= 0 ? ld_status(status + (size_t)(p - j) * RS_RADIX + d)
+                                   : (unsigned long long)ST_PREFIX;
+#pragma unroll
+            for (int j = 0; j < RS_LOOKBACK; j++) {
+                if (!done) {
+                    unsigned long long s = sv[j];
+                    uint32_t spins = 0;
+                    while ((s >> 62) == 0) {
+                        if (++spins > SPIN_LIMIT) { raise_err(err, ERRF_TIMEOUT); s = ST_PREFIX; break; }
+                        s = ld_status(status + (size_t)(p - j) * RS_RADIX + d);
+                    }
+                    excl += s & ST_MASK;
+                    done = (s & ST_PREFIX) != 0;
+                }
             }
-            excl += s & ST_MASK;
-            if (s & ST_PREFIX) break;
-            p--;
+            p -= RS_LOOKBACK;
         }
         atomicExch(&st[d], (unsigned long long)(ST_PREFIX | (excl + cnt)));
         s_glob[d] = bucket_base[d] + (uint32_t)excl;
@@ -193,10 +260,12 @@ k_onesweep_t(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 }
 
 // the (key, value) form used by factor construction
-constexpr auto k_onesweep = k_onesweep_t<true>;
+constexpr auto k_onesweep = k_onesweep_t<true, false>;
 
 constexpr size_t RS_SMEM = (size_t)RS_TILE * 8 + (size_t)RS_TILE * 4 +
                            (size_t)RS_WARPS * RS_RADIX * 4 + 2 * RS_RADIX * 4 + 8 * 4;
+// keys only: no staged values (5 CTAs fit an SM's shared memory)
+constexpr size_t RS_SMEM_K = (size_t)RS_TILE * 8 + (size_t)RS_WARPS * RS_RADIX * 4 + 2 * RS_RADIX * 4 + 8 * 4;
 
 }  // namespace
 
@@ -221,7 +290,7 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
                                 c.stream));
     int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
     if (hist_blocks < 1) hist_blocks = 1;
-    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_digit_hist<false><<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, PackSrc{}, n, 0, passes, hist); c.launches++;
     k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
     uint64_t *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
@@ -229,7 +298,7 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
         GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
                                     c.stream));
         k_onesweep<<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
-            ka, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+            ka, PackSrc{}, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
         GJ_CUDA_TRY(cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -267,7 +336,7 @@ cudaError_t radix_sort_u64_u32_in(Ctx &c, uint64_t *keys, uint32_t *vals, int64_
                                 c.stream));
     int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
     if (hist_blocks < 1) hist_blocks = 1;
-    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_digit_hist<false><<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, PackSrc{}, n, 0, passes, hist); c.launches++;
     k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
     uint64_t *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
@@ -275,7 +344,7 @@ cudaError_t radix_sort_u64_u32_in(Ctx &c, uint64_t *keys, uint32_t *vals, int64_
         GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
                                     c.stream));
         k_onesweep<<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
-            ka, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+            ka, PackSrc{}, va, kb, vb, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
         GJ_CUDA_TRY(cudaGetLastError());
         std::swap(ka, kb);
         std::swap(va, vb);
@@ -294,7 +363,7 @@ namespace gj {
 // Sets the keys-only sort kernel's shared-memory limit; call once before
 // any capture of radix_sort_keys_u64_in.
 cudaError_t radix_sort_keys_prepare() {
-    return cudaFuncSetAttribute(k_onesweep_t<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_onesweep_t<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)RS_SMEM);
 }
 
@@ -314,14 +383,14 @@ cudaError_t radix_sort_keys_u64_in(Ctx &c, uint64_t *keys, int64_t n, int bits, 
                                 c.stream));
     int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
     if (hist_blocks < 1) hist_blocks = 1;
-    k_digit_hist<<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, n, passes, hist); c.launches++;
+    k_digit_hist<false><<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, PackSrc{}, n, 0, passes, hist); c.launches++;
     k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
     uint64_t *ka = keys, *kb = k2;
     for (int p = 0; p < passes; p++) {
         GJ_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * tiles * RS_RADIX,
                                     c.stream));
-        k_onesweep_t<false><<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
-            ka, nullptr, kb, nullptr, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
+        k_onesweep_t<false, false><<<(unsigned)tiles, RS_THREADS, RS_SMEM, c.stream>>>(
+            ka, PackSrc{}, nullptr, kb, nullptr, n, 8 * p, hist + p * RS_RADIX, counters + p, status, c.err); c.launches++;
         GJ_CUDA_TRY(cudaGetLastError());
         std::swap(ka, kb);
     }
@@ -331,3 +400,85 @@ cudaError_t radix_sort_keys_u64_in(Ctx &c, uint64_t *keys, int64_t n, int bits, 
 }
 
 }  // namespace gj
+
+namespace gj {
+
+cudaError_t radix_sort_words(Ctx &c, const PackSrc *pack, uint64_t *keys, uint64_t *alt,
+                             uint32_t *vals, uint32_t *valt, int64_t n, int lo_bit, int bits,
+                             uint64_t **kres, uint32_t **vres) {
+    *kres = keys;
+    if (vres) *vres = vals;
+    if (n > 0x7fffffffLL || bits < 0 || lo_bit < 0 || lo_bit + bits > 64) return cudaErrorInvalidValue;
+    const bool with_vals = vals != nullptr;
+    const int passes = (bits + 7) / 8;
+    if (n == 0) return cudaSuccess;
+    if (passes == 0 || n == 1) {
+        // nothing to order: the words (and row ids) in input order
+        if (pack) {
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, RS_THREADS), (int64_t)c.num_sms * 16));
+            k_pack_words<<<grid, RS_THREADS, 0, c.stream>>>(*pack, n, keys, vals); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+        }
+        return cudaSuccess;
+    }
+    const size_t smem = with_vals ? RS_SMEM : RS_SMEM_K;
+    if (with_vals) {
+        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep_t<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep_t<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    } else {
+        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep_t<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GJ_CUDA_TRY(cudaFuncSetAttribute(k_onesweep_t<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    const int64_t tiles = ceil_div(n, RS_TILE);
+    uint32_t *hist = nullptr;
+    unsigned long long *status = nullptr;
+    GJ_CUDA_TRY(dalloc(c, &hist, RS_MAX_PASSES * RS_RADIX + RS_MAX_PASSES));
+    GJ_CUDA_TRY(dalloc(c, &status, (size_t)tiles * RS_RADIX));
+    uint32_t *counters = hist + RS_MAX_PASSES * RS_RADIX;
+    GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + RS_MAX_PASSES), c.stream));
+    const PackSrc ps = pack ? *pack : PackSrc{};
+    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
+    if (hist_blocks < 1) hist_blocks = 1;
+    if (pack)
+        k_digit_hist<true><<<hist_blocks, RS_THREADS, 0, c.stream>>>(nullptr, ps, n, lo_bit, passes, hist);
+    else
+        k_digit_hist<false><<<hist_blocks, RS_THREADS, 0, c.stream>>>(keys, ps, n, lo_bit, passes, hist);
+    c.launches++;
+    k_hist_to_base<<<passes, RS_RADIX, 0, c.stream>>>(hist); c.launches++;
+    uint64_t *ka = keys, *kb = alt;
+    uint32_t *va = vals, *vb = valt;
+    for (int p = 0; p < passes; p++) {
+        unsigned long long *st = status;   // one pass's lookback state at a time
+        GJ_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(unsigned long long) * tiles * RS_RADIX, c.stream));
+        const int shift = lo_bit + 8 * p;
+        // the first pass of a packed sort reads the columns and writes into
+        // `alt`; later passes ping-pong
+        if (with_vals) {
+            if (p == 0 && pack)
+                k_onesweep_t<true, true><<<(unsigned)tiles, RS_THREADS, smem, c.stream>>>(
+                    nullptr, ps, nullptr, kb, vb, n, shift, hist + p * RS_RADIX, counters + p, st, c.err);
+            else
+                k_onesweep_t<true, false><<<(unsigned)tiles, RS_THREADS, smem, c.stream>>>(
+                    ka, ps, va, kb, vb, n, shift, hist + p * RS_RADIX, counters + p, st, c.err);
+        } else {
+            if (p == 0 && pack)
+                k_onesweep_t<false, true><<<(unsigned)tiles, RS_THREADS, smem, c.stream>>>(
+                    nullptr, ps, nullptr, kb, nullptr, n, shift, hist + p * RS_RADIX, counters + p, st, c.err);
+            else
+                k_onesweep_t<false, false><<<(unsigned)tiles, RS_THREADS, smem, c.stream>>>(
+                    ka, ps, nullptr, kb, nullptr, n, shift, hist + p * RS_RADIX, counters + p, st, c.err);
+        }
+        c.launches++;
+        GJ_CUDA_TRY(cudaGetLastError());
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    *kres = ka;
+    if (vres) *vres = va;
+    dfree(c, hist);
+    dfree(c, status);
+    return cudaSuccess;
+}
+
+}  // namespace gj
+

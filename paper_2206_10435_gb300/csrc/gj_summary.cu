@@ -26,8 +26,21 @@
 // down_t(g) (x) cnt[g] (x) prod_{c' != c} msg_c'.  mult[g] = w[g] (x) down(g)
 // is the number of result tuples using group g, i.e. the marginal of g's key
 // tuple over the join result (Section 1.2, "Why PGMs").
+//
+// Kernels.  Per relation, the whole upward step is one single-pass scan
+// (decoupled lookback) whose element is (w, live, head): w computed from the
+// counts and the children's messages, head marking the first group of a
+// separator segment, live = w > 0.  Its combine is a segmented saturating sum
+// of w next to plain counts of heads and live groups, so one pass yields the
+// in-segment offsets, the messages (segment sums), the segment numbering
+// and the compaction of the live groups the desummariser walks.  Per
+// relation, the downward step is one kernel: mult, and every child's down
+// message accumulated exactly by non-returning 64-bit atomic adds of the
+// contributions' 32-bit halves (the true sum is recovered in 128 bits, so
+// saturation is exact).
 #include <algorithm>
 
+#include "gj_lookback.cuh"
 #include "gj_state.cuh"
 
 namespace gj {
@@ -44,14 +57,6 @@ struct KeyCols {
     const int32_t *col[MAX_KEYS];
 };
 
-struct ChildSet {
-    int n;
-    const uint32_t *link[MAX_REL];
-    const uint64_t *msg[MAX_REL];
-    unsigned long long *lo[MAX_REL];
-    unsigned int *carry[MAX_REL];
-};
-
 inline int grid_for(Ctx &c, int64_t n) {
     int64_t b = ceil_div(n, ST);
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)c.num_sms * 16));
@@ -60,34 +65,8 @@ inline int grid_for(Ctx &c, int64_t n) {
 #define GRID_LOOP(i, n) \
     for (int64_t i = (int64_t)blockIdx.x * ST + threadIdx.x; i < (n); i += (int64_t)gridDim.x * ST)
 
-__global__ void k_seg_heads(KeyCols sep, int64_t G, uint8_t *heads) {
-    GRID_LOOP(g, G) {
-        uint8_t h = (g == 0);
-        if (!h)
-            for (int c = 0; c < sep.ncol; c++)
-                if (sep.col[c][g] != sep.col[c][g - 1]) { h = 1; break; }
-        heads[g] = h;
-    }
-}
-
-__global__ void k_seg_finalize(const uint8_t *heads, const uint32_t *excl, int64_t G,
-                               const uint32_t *S_dev, uint32_t *seg_id, uint32_t *seg_first) {
-    GRID_LOOP(g, G) {
-        uint32_t s = excl[g] + heads[g] - 1u;
-        seg_id[g] = s;
-        if (heads[g]) seg_first[s] = (uint32_t)g;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) seg_first[*S_dev] = (uint32_t)G;
-}
-
 __global__ void k_fill_u32(uint32_t *p, int64_t n, uint32_t v) {
     GRID_LOOP(i, n) p[i] = v;
-}
-
-__global__ void k_dense_fill(const int32_t *child_key, const uint32_t *seg_first,
-                             const uint32_t *S_dev, int32_t mn, uint32_t *dense) {
-    const int64_t S = *S_dev;
-    GRID_LOOP(s, S) dense[(uint32_t)child_key[seg_first[s]] - (uint32_t)mn] = (uint32_t)s;
 }
 
 __global__ void k_link_dense(const int32_t *parent_key, int64_t Gp, int32_t mn, uint64_t range,
@@ -126,75 +105,378 @@ __global__ void k_link_search(KeyCols pk, int64_t Gp, KeyCols ck, const uint32_t
     }
 }
 
-__global__ void k_weights(const uint32_t *gstart, int64_t G, ChildSet ch, uint64_t *w) {
-    GRID_LOOP(g, G) {
-        uint64_t v = (uint64_t)(gstart[g + 1] - gstart[g]);
-        for (int i = 0; i < ch.n; i++) {
-            uint32_t s = ch.link[i][g];
-            v = sat_mul(v, s == NONE ? 0ull : ch.msg[i][s]);
-        }
-        w[g] = v;
-    }
+// ------------------------------------------------------------ upward scan
+// Scan state of a run of groups: v = saturating sum of w since the last
+// segment head (inclusive of everything when there is none), nh = heads,
+// nl = live groups.  (a) . (b) = (b.nh ? b.v : a.v (+) b.v, a.nh + b.nh,
+// a.nl + b.nl): associative, not commutative.
+struct UpState {
+    uint64_t v;
+    uint32_t nh, nl;
+};
+
+__device__ __forceinline__ UpState up_op(const UpState &a, const UpState &b) {
+    UpState r;
+    r.v = b.nh ? b.v : sat_add(a.v, b.v);
+    r.nh = a.nh + b.nh;
+    r.nl = a.nl + b.nl;
+    return r;
 }
 
-// contributions of t's groups to every child's down message
-__global__ void k_down_contrib(const uint32_t *gstart, int64_t G, const uint64_t *t_down,
-                               const uint32_t *t_seg, ChildSet ch) {
-    GRID_LOOP(g, G) {
-        uint64_t base = (uint64_t)(gstart[g + 1] - gstart[g]);
-        if (t_down) base = sat_mul(base, t_down[t_seg[g]]);
-        if (base == 0) continue;
-        for (int i = 0; i < ch.n; i++) {
-            uint32_t s = ch.link[i][g];
-            if (s == NONE) continue;
-            uint64_t x = base;
-            for (int j = 0; j < ch.n && x; j++) {
-                if (j == i) continue;
-                uint32_t sj = ch.link[j][g];
-                x = sat_mul(x, sj == NONE ? 0ull : ch.msg[j][sj]);
+__device__ __forceinline__ UpState up_shfl_up(const UpState &x, int d) {
+    UpState r;
+    r.v = __shfl_up_sync(0xffffffffu, x.v, d);
+    r.nh = __shfl_up_sync(0xffffffffu, x.nh, d);
+    r.nl = __shfl_up_sync(0xffffffffu, x.nl, d);
+    return r;
+}
+
+__device__ __forceinline__ UpState up_shfl_down(const UpState &x, int d) {
+    UpState r;
+    r.v = __shfl_down_sync(0xffffffffu, x.v, d);
+    r.nh = __shfl_down_sync(0xffffffffu, x.nh, d);
+    r.nl = __shfl_down_sync(0xffffffffu, x.nl, d);
+    return r;
+}
+
+__device__ __forceinline__ UpState up_shfl(const UpState &x, int l) {
+    UpState r;
+    r.v = __shfl_sync(0xffffffffu, x.v, l);
+    r.nh = __shfl_sync(0xffffffffu, x.nh, l);
+    r.nl = __shfl_sync(0xffffffffu, x.nl, l);
+    return r;
+}
+
+// A tile's published state: flag, heads and live count in one word (the
+// counts are below 2^31), the sum in the other, moved as one 16-byte access.
+__device__ __forceinline__ void up_put(ulonglong2 *s, uint32_t f, const UpState &x) {
+    const unsigned long long a = (unsigned long long)f | ((unsigned long long)x.nh << 2) |
+                                 ((unsigned long long)x.nl << 33);
+    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(s), "l"(a),
+                 "l"((unsigned long long)x.v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void up_get(const ulonglong2 *s, uint32_t &f, UpState &x) {
+    unsigned long long a, b;
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(s) : "memory");
+    f = (uint32_t)(a & 3u);
+    x.nh = (uint32_t)((a >> 2) & 0x7fffffffu);
+    x.nl = (uint32_t)(a >> 33);
+    x.v = b;
+}
+
+// Decoupled lookback by one warp for the ordered (non-commutative) combine:
+// the window of 32 predecessors is folded in tile order by a shuffle-down
+// tree.  Polls are bounded by SPIN_LIMIT (ERRF_TIMEOUT on expiry, the
+// predecessor then counts as an empty prefix).
+__device__ UpState up_lookback(ulonglong2 *st, uint32_t tile, const UpState &agg, int lane,
+                               uint32_t *err) {
+    const UpState zero{0ull, 0u, 0u};
+    if (tile == 0) {
+        if (lane == 0) up_put(&st[0], ST_P, agg);
+        return zero;
+    }
+    if (lane == 0) up_put(&st[tile], ST_A, agg);
+    UpState carry = zero;
+    int64_t p = (int64_t)tile - 1;
+    for (;;) {
+        const int64_t q = p - 31 + lane;
+        uint32_t f = ST_P;
+        UpState v = zero;
+        if (q >= 0) {
+            uint32_t spins = 0;
+            for (;;) {
+                up_get(&st[q], f, v);
+                if (f) break;
+                if (++spins > SPIN_LIMIT) {
+                    raise_err(err, ERRF_TIMEOUT);
+                    f = ST_P;
+                    v = zero;
+                    break;
+                }
             }
-            if (x == 0) continue;
-            // exact sum modulo 2^64 plus a wrap counter: saturates iff the
-            // true sum is >= 2^64 - 1, with native 64-bit atomics
-            if (x == SAT) { atomicOr(&ch.carry[i][s], 1u); continue; }
-            unsigned long long old = atomicAdd(&ch.lo[i][s], (unsigned long long)x);
-            if (old + x < old) atomicOr(&ch.carry[i][s], 1u);
+        }
+        const uint32_t pm = __ballot_sync(0xffffffffu, f == ST_P);
+        const int hi = pm ? 31 - __clz((int)pm) : 0;
+        UpState x = lane >= hi ? v : zero;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const UpState y = up_shfl_down(x, d);
+            if (lane + d < 32) x = up_op(x, y);
+        }
+        x = up_shfl(x, 0);
+        carry = up_op(x, carry);
+        if (pm) break;
+        p -= 32;
+    }
+    if (lane == 0) up_put(&st[tile], ST_P, up_op(carry, agg));
+    return carry;
+}
+
+struct UpSpec {
+    int64_t G;
+    const uint32_t *gstart;            // counts: gstart[g + 1] - gstart[g]
+    int nch;
+    const uint32_t *link[MAX_REL];     // children's links and messages
+    const uint64_t *msg[MAX_REL];
+    int seg;                           // segmented by the separator (non-root)
+    KeyCols sep;                       // separator key columns (heads)
+    // outputs
+    uint64_t *w, *off;
+    uint64_t *msg_out;                 // [S] segment sums (non-root)
+    uint32_t *seg_id, *seg_first;      // [G], [S+1] (non-root)
+    uint32_t *S_dev;
+    uint32_t *lgid;                    // live groups: [L]
+    uint64_t *loff, *lw;
+    uint32_t *lseg_first;              // [S+1] (non-root)
+    uint32_t *L_dev;
+    uint64_t *total;                   // root: sum of all w
+    // dense link table of this relation's segments (one separator column of
+    // small range): dense[key - dense_mn] = segment
+    uint32_t *dense;
+    const int32_t *dense_key;
+    int32_t dense_mn;
+    // lookback
+    ulonglong2 *status;
+    uint32_t *counter;
+    uint32_t *err;
+};
+
+constexpr int UP_ITEMS = 8;
+constexpr int UP_TILE = ST * UP_ITEMS;
+
+// shared-memory slot of element e: one pad slot per 16 (64-bit arrays) or
+// 32 (32-bit arrays) elements keeps both the coalesced (warp on 32
+// consecutive elements) and the per-thread (thread on UP_ITEMS consecutive
+// elements) phases free of bank conflicts
+__device__ __forceinline__ int p64(int e) { return e + (e >> 4); }
+__device__ __forceinline__ int p32(int e) { return e + (e >> 5); }
+constexpr int UP_S64 = UP_TILE + UP_TILE / 16;
+constexpr int UP_S32 = UP_TILE + UP_TILE / 32;
+constexpr size_t UP_SMEM = 2 * (size_t)UP_S64 * 8 + 2 * (size_t)UP_S32 * 4 + UP_TILE;
+
+__device__ __forceinline__ bool sep_head(const KeyCols &sep, int64_t g) {
+    if (g == 0) return true;
+    for (int c = 0; c < sep.ncol; c++)
+        if (__ldg(sep.col[c] + g) != __ldg(sep.col[c] + g - 1)) return true;
+    return false;
+}
+
+__global__ void __launch_bounds__(ST)
+k_up_scan(UpSpec s) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *s_w = (uint64_t *)smem;                 // the element's w
+    uint64_t *s_xv = s_w + UP_S64;                    // exclusive v
+    uint32_t *s_xh = (uint32_t *)(s_xv + UP_S64);     // exclusive heads
+    uint32_t *s_xl = s_xh + UP_S32;                   // exclusive live groups
+    uint8_t *s_h = (uint8_t *)(s_xl + UP_S32);        // head flag
+    __shared__ UpState s_warp[ST / 32];
+    __shared__ UpState s_carry;
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(s.counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t base = (int64_t)tile * UP_TILE;
+    if (base >= s.G) return;
+    const int tile_n = (int)min((int64_t)UP_TILE, s.G - base);
+    // elements, coalesced: w = cnt (x) children's messages; head; (live = w > 0)
+    for (int e = tid; e < UP_TILE; e += ST) {
+        const int64_t g = base + e;
+        uint64_t w = 0;
+        uint8_t h = 0;
+        if (e < tile_n) {
+            w = (uint64_t)(__ldg(s.gstart + g + 1) - __ldg(s.gstart + g));
+            for (int i = 0; i < s.nch; i++) {
+                const uint32_t l = __ldg(s.link[i] + g);
+                w = sat_mul(w, l == NONE ? 0ull : __ldg((const unsigned long long *)s.msg[i] + l));
+            }
+            h = s.seg ? sep_head(s.sep, g) : 0;
+        }
+        s_w[p64(e)] = w;
+        s_h[e] = h;
+    }
+    __syncthreads();
+    // each thread: UP_ITEMS consecutive elements
+    UpState run{0ull, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; i++) {
+        const int e = tid * UP_ITEMS + i;
+        const UpState x{s_w[p64(e)], (uint32_t)s_h[e], s_w[p64(e)] != 0 ? 1u : 0u};
+        run = up_op(run, x);
+    }
+    // warp inclusive scan of the threads' states, in order
+    UpState inc = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const UpState y = up_shfl_up(inc, d);
+        if (lane >= d) inc = up_op(y, inc);
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    UpState ex = up_shfl_up(inc, 1);
+    if (lane == 0) ex = UpState{0ull, 0u, 0u};
+    __syncthreads();
+    UpState before{0ull, 0u, 0u};
+    for (int w = 0; w < warp; w++) before = up_op(before, s_warp[w]);
+    if (warp == ST / 32 - 1) {
+        // the tile's aggregate (last warp), then its carry-in
+        UpState agg{0ull, 0u, 0u};
+        for (int w = 0; w < ST / 32; w++) agg = up_op(agg, s_warp[w]);
+        const UpState carry = up_lookback(s.status, tile, agg, lane, s.err);
+        if (lane == 0) {
+            s_carry = carry;
+            if (base + UP_TILE >= s.G) {   // the last tile: totals
+                const UpState all = up_op(carry, agg);
+                if (s.seg) {
+                    *s.S_dev = all.nh;
+                    s.seg_first[all.nh] = (uint32_t)s.G;
+                    s.lseg_first[all.nh] = all.nl;
+                } else if (s.total) {
+                    *s.total = all.v;
+                }
+                *s.L_dev = all.nl;
+            }
+        }
+    }
+    __syncthreads();
+    // exclusive state of each of the thread's elements
+    UpState x = up_op(up_op(s_carry, before), ex);
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; i++) {
+        const int e = tid * UP_ITEMS + i;
+        s_xv[p64(e)] = x.v;
+        s_xh[p32(e)] = x.nh;
+        s_xl[p32(e)] = x.nl;
+        const UpState y{s_w[p64(e)], (uint32_t)s_h[e], s_w[p64(e)] != 0 ? 1u : 0u};
+        x = up_op(x, y);
+    }
+    __syncthreads();
+    // outputs, coalesced
+    for (int e = tid; e < tile_n; e += ST) {
+        const int64_t g = base + e;
+        const uint64_t w = s_w[p64(e)];
+        const bool h = s_h[e] != 0;
+        const uint64_t xv = s_xv[p64(e)];
+        const uint32_t xl = s_xl[p32(e)];
+        const uint64_t off = h ? 0ull : xv;
+        s.w[g] = w;
+        s.off[g] = off;
+        if (s.seg) {
+            const uint32_t sid = s_xh[p32(e)] + (h ? 1u : 0u) - 1u;
+            s.seg_id[g] = sid;
+            if (h) {
+                s.seg_first[sid] = (uint32_t)g;
+                s.lseg_first[sid] = xl;
+                if (s.dense) s.dense[(uint32_t)__ldg(s.dense_key + g) - (uint32_t)s.dense_mn] = sid;
+            }
+            // the segment's last group writes its message
+            const bool last = (g + 1 == s.G) || (e + 1 < tile_n ? s_h[e + 1] != 0 : sep_head(s.sep, g + 1));
+            if (last) s.msg_out[sid] = sat_add(off, w);
+        }
+        if (w != 0) {
+            s.lgid[xl] = (uint32_t)g;
+            s.loff[xl] = off;
+            s.lw[xl] = w;
         }
     }
 }
 
-__global__ void k_down_finalize(const unsigned long long *lo, const unsigned int *carry,
-                                const uint32_t *S_dev, uint64_t *down) {
-    const int64_t S = *S_dev;
-    GRID_LOOP(s, S) down[s] = (carry[s] || lo[s] == SAT) ? SAT : (uint64_t)lo[s];
+// ------------------------------------------------------------ downward
+// A child's down message, accumulated exactly: lo = sum of the
+// contributions' low 32-bit halves, hi = sum of their high halves (fewer
+// than 2^31 contributions, so neither wraps), sat = a contribution was
+// SAT.  The value is hi * 2^32 + lo, saturated at SAT.
+struct DownAcc {
+    unsigned long long *lo, *hi;
+    unsigned int *sat;
+};
+
+__device__ __forceinline__ uint64_t down_value(const DownAcc &a, uint32_t s) {
+    if (a.sat[s]) return SAT;
+    const uint64_t lo = a.lo[s], hi = a.hi[s];
+    const uint64_t top = hi + (lo >> 32);
+    if (top >> 32) return SAT;
+    const uint64_t v = (top << 32) | (lo & 0xffffffffull);
+    return v == SAT ? SAT : v;
 }
 
-__global__ void k_mult(const uint64_t *w, const uint64_t *t_down, const uint32_t *t_seg, int64_t G,
-                       uint64_t *mult) {
-    GRID_LOOP(g, G) mult[g] = t_down ? sat_mul(w[g], t_down[t_seg[g]]) : w[g];
-}
+struct DownSpec {
+    int64_t G;
+    const uint32_t *gstart;
+    const uint64_t *w;
+    uint64_t *mult;
+    // this relation's own down message (non-root)
+    int has_down;
+    DownAcc self;
+    const uint32_t *seg_id, *seg_first;
+    uint64_t *down_out;                // [S] the finished values
+    // children
+    int nch;
+    const uint32_t *link[MAX_REL];
+    const uint64_t *msg[MAX_REL];
+    DownAcc acc[MAX_REL];
+};
 
-__global__ void k_nonzero(const uint64_t *w, int64_t G, uint8_t *f) {
-    GRID_LOOP(g, G) f[g] = w[g] != 0;
-}
-
-__global__ void k_live_compact(const uint8_t *f, const uint32_t *lidx, const uint64_t *w,
-                               const uint64_t *off, int64_t G, uint32_t *lgid, uint64_t *loff,
-                               uint64_t *lw) {
-    GRID_LOOP(g, G) {
-        if (!f[g]) continue;
-        uint32_t h = lidx[g];
-        lgid[h] = (uint32_t)g;
-        loff[h] = off[g];
-        lw[h] = w[g];
+// NCH > 0: exactly NCH children (register arrays); NCH < 0: s.nch children
+template <int NCH>
+__global__ void __launch_bounds__(ST)
+k_down(DownSpec s) {
+    constexpr int CAP = NCH >= 0 ? (NCH > 0 ? NCH : 1) : MAX_REL;
+    const int nch = NCH >= 0 ? NCH : s.nch;
+    GRID_LOOP(g, s.G) {
+        uint64_t base = (uint64_t)(__ldg(s.gstart + g + 1) - __ldg(s.gstart + g));
+        const uint64_t w = __ldg((const unsigned long long *)s.w + g);
+        if (s.has_down) {
+            const uint32_t sid = __ldg(s.seg_id + g);
+            const uint64_t d = down_value(s.self, sid);
+            if (__ldg(s.seg_first + sid) == (uint32_t)g) s.down_out[sid] = d;
+            base = sat_mul(base, d);
+            s.mult[g] = sat_mul(w, d);
+        } else {
+            s.mult[g] = w;
+        }
+        if constexpr (NCH != 0) {
+            if (base == 0) continue;
+            uint32_t l[CAP];
+            uint64_t m[CAP];
+#pragma unroll
+            for (int i = 0; i < CAP; i++) {
+                if (i >= nch) break;
+                l[i] = __ldg(s.link[i] + g);
+                m[i] = l[i] == NONE ? 0ull : __ldg((const unsigned long long *)s.msg[i] + l[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < CAP; i++) {
+                if (i >= nch) break;
+                if (l[i] == NONE) continue;
+                uint64_t x = base;
+#pragma unroll
+                for (int j = 0; j < CAP; j++)
+                    if (j < nch && j != i) x = sat_mul(x, m[j]);
+                if (x == 0) continue;
+                if (x == SAT) {
+                    atomicOr(s.acc[i].sat + l[i], 1u);
+                    continue;
+                }
+                // results unused: compiled to fire-and-forget reductions
+                atomicAdd(s.acc[i].lo + l[i], (unsigned long long)(x & 0xffffffffull));
+                if (x >> 32) atomicAdd(s.acc[i].hi + l[i], (unsigned long long)(x >> 32));
+            }
+        }
     }
 }
 
-__global__ void k_live_segs(const uint32_t *seg_first, const uint32_t *lidx,
-                            const uint32_t *S_dev, const uint32_t *L_dev, uint32_t *lseg_first) {
-    const int64_t S = *S_dev;
-    GRID_LOOP(s, S) lseg_first[s] = lidx[seg_first[s]];
-    if (blockIdx.x == 0 && threadIdx.x == 0) lseg_first[S] = *L_dev;
+void launch_down(Ctx &c, int grid, const DownSpec &d) {
+    switch (d.nch) {
+        case 0: k_down<0><<<grid, ST, 0, c.stream>>>(d); break;
+        case 1: k_down<1><<<grid, ST, 0, c.stream>>>(d); break;
+        case 2: k_down<2><<<grid, ST, 0, c.stream>>>(d); break;
+        case 3: k_down<3><<<grid, ST, 0, c.stream>>>(d); break;
+        case 4: k_down<4><<<grid, ST, 0, c.stream>>>(d); break;
+        default: k_down<-1><<<grid, ST, 0, c.stream>>>(d); break;
+    }
+    c.launches++;
 }
 
 inline KeyCols key_cols(const QRel &q, const std::vector<int> &cols) {
@@ -204,57 +486,13 @@ inline KeyCols key_cols(const QRel &q, const std::vector<int> &cols) {
     return k;
 }
 
-cudaError_t build_segments(Ctx &c, QRel &t) {
-    const int64_t G = t.F->G;
-    GJ_CUDA_TRY(dalloc(c, &t.seg_id, G));
-    GJ_CUDA_TRY(dalloc(c, &t.seg_first, G + 1));
-    GJ_CUDA_TRY(dalloc(c, &t.S_dev, 1));
-    uint8_t *heads = nullptr;
-    uint32_t *excl = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &heads, G));
-    GJ_CUDA_TRY(dalloc(c, &excl, G));
-    k_seg_heads<<<grid_for(c, G), ST, 0, c.stream>>>(key_cols(t, t.sep_cols), G, heads); c.launches++;
-    GJ_CUDA_TRY(scan_u32(c, nullptr, heads, excl, G, t.S_dev));
-    k_seg_finalize<<<grid_for(c, G), ST, 0, c.stream>>>(heads, excl, G, t.S_dev, t.seg_id, t.seg_first); c.launches++;
-    GJ_CUDA_TRY(cudaGetLastError());
-    dfree(c, heads);
-    dfree(c, excl);
-    return cudaSuccess;
-}
-
-// link[g] for every group g of parent t: segment of child ch with equal
-// separator values, or NONE
-cudaError_t build_link(Ctx &c, QRel &t, QRel &ch, uint32_t **link_out) {
-    const int64_t Gp = t.F->G;
-    uint32_t *link = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &link, Gp));
-    *link_out = link;
-    if (Gp == 0) return cudaSuccess;
-    if (ch.F->G == 0) {
-        k_fill_u32<<<grid_for(c, Gp), ST, 0, c.stream>>>(link, Gp, NONE); c.launches++;
-        return cudaGetLastError();
-    }
-    if (ch.sep_cols.size() == 1) {
-        int col = ch.sep_cols[0];
-        int64_t range = (int64_t)ch.R->kmax[col] - (int64_t)ch.R->kmin[col] + 1;
-        if (range <= DENSE_MAX && range <= 4 * (ch.F->G + Gp) + 4096) {
-            uint32_t *dense = nullptr;
-            GJ_CUDA_TRY(dalloc(c, &dense, range));
-            GJ_CUDA_TRY(cudaMemsetAsync(dense, 0xFF, sizeof(uint32_t) * range, c.stream));
-            k_dense_fill<<<grid_for(c, ch.F->G), ST, 0, c.stream>>>(
-                ch.F->gkey + (int64_t)col * ch.F->G, ch.seg_first, ch.S_dev, ch.R->kmin[col], dense); c.launches++;
-            k_link_dense<<<grid_for(c, Gp), ST, 0, c.stream>>>(
-                t.F->gkey + (int64_t)ch.sep_cols_parent[0] * Gp, Gp, ch.R->kmin[col],
-                (uint64_t)range, dense, link); c.launches++;
-            GJ_CUDA_TRY(cudaGetLastError());
-            dfree(c, dense);
-            return cudaSuccess;
-        }
-    }
-    k_link_search<<<grid_for(c, Gp), ST, 0, c.stream>>>(key_cols(t, ch.sep_cols_parent), Gp,
-                                                        key_cols(ch, ch.sep_cols), ch.seg_first,
-                                                        ch.S_dev, link); c.launches++;
-    return cudaGetLastError();
+// Whether the parent's link to child ch goes through a dense table over the
+// child's single separator column, and that table's range.
+bool dense_link(const QRel &t, const QRel &ch, int64_t *range) {
+    if (ch.sep_cols.size() != 1 || ch.F->G == 0 || t.F->G == 0) return false;
+    const int col = ch.sep_cols[0];
+    *range = (int64_t)ch.R->kmax[col] - (int64_t)ch.R->kmin[col] + 1;
+    return *range <= DENSE_MAX && *range <= 4 * (ch.F->G + t.F->G) + 4096;
 }
 
 }  // namespace
@@ -289,6 +527,39 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
     Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;
+    // one block of scratch for the whole summary: every relation's lookback
+    // state, every dense link table, every child's down accumulators, |Q|
+    std::vector<int64_t> st_off(q.k), dense_off(q.k, -1), dense_range(q.k, 0), acc_off(q.k, -1);
+    size_t bytes = 64;
+    for (int i = 0; i < q.k; i++) {
+        st_off[i] = (int64_t)bytes;
+        bytes += 16 * (size_t)(ceil_div(std::max<int64_t>(q.r[i].F->G, 1), UP_TILE) + 1);
+    }
+    const size_t zero_end = bytes;   // lookback state: cleared to 0
+    for (int i = 1; i < q.k; i++) {
+        const QRel &ch = q.r[i];
+        int64_t range = 0;
+        if (dense_link(q.r[ch.parent], ch, &range)) {
+            dense_off[i] = (int64_t)bytes;
+            dense_range[i] = range;
+            bytes += ((size_t)range * 4 + 15) & ~(size_t)15;
+        }
+    }
+    const size_t dense_end = bytes;  // dense tables: cleared to 0xFF (NONE)
+    for (int i = 1; i < q.k; i++) {
+        acc_off[i] = (int64_t)bytes;
+        bytes += (size_t)std::max<int64_t>(q.r[i].F->G, 1) * 20;
+        bytes = (bytes + 15) & ~(size_t)15;
+    }
+    char *scratch = nullptr;
+    auto acc_of = [&](int i) {
+        const int64_t S = std::max<int64_t>(q.r[i].F->G, 1);
+        DownAcc a;
+        a.lo = (unsigned long long *)(scratch + acc_off[i]);
+        a.hi = a.lo + S;
+        a.sat = (unsigned int *)(a.hi + S);
+        return a;
+    };
 #define TRY(x)                                                 \
     do {                                                       \
         e = (x);                                               \
@@ -298,100 +569,122 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
         }                                                      \
     } while (0)
     {
-        // segments of every non-root relation, then links parent -> child
-        for (int i = 1; i < q.k; i++) TRY(build_segments(c, q.r[i]));
-        for (int i = 0; i < q.k; i++) {
-            QRel &t = q.r[i];
-            t.link.assign(t.children.size(), nullptr);
-            for (size_t ci = 0; ci < t.children.size(); ci++)
-                TRY(build_link(c, t, q.r[t.children[ci]], &t.link[ci]));
-        }
-        // upward, leaves to root (reverse preorder)
-        uint64_t *total_dev = nullptr;
-        TRY(dalloc(c, &total_dev, 1));
+        TRY(dalloc_bytes(c, (void **)&scratch, bytes));
+        TRY(cudaMemsetAsync(scratch, 0, zero_end, c.stream));
+        if (dense_end > zero_end) TRY(cudaMemsetAsync(scratch + zero_end, 0xFF, dense_end - zero_end, c.stream));
+        if (bytes > dense_end) TRY(cudaMemsetAsync(scratch + dense_end, 0, bytes - dense_end, c.stream));
+        uint64_t *total_dev = (uint64_t *)scratch;
+        TRY(cudaFuncSetAttribute(k_up_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UP_SMEM));
+        // upward, leaves to root (reverse preorder): links to the children
+        // (whose segments exist by now), then the relation's scan
         for (int pi = q.k - 1; pi >= 0; pi--) {
-            QRel &t = q.r[q.pre[pi]];
+            const int ti = q.pre[pi];
+            QRel &t = q.r[ti];
             const int64_t G = t.F->G;
-            ChildSet cs{};
-            cs.n = (int)t.children.size();
-            for (int ci = 0; ci < cs.n; ci++) {
-                cs.link[ci] = t.link[ci];
-                cs.msg[ci] = q.r[t.children[ci]].msg;
+            t.link.assign(t.children.size(), nullptr);
+            for (size_t ci = 0; ci < t.children.size(); ci++) {
+                const int chi = t.children[ci];
+                QRel &ch = q.r[chi];
+                TRY(dalloc(c, &t.link[ci], G));
+                if (G == 0) continue;
+                if (ch.F->G == 0) {
+                    k_fill_u32<<<grid_for(c, G), ST, 0, c.stream>>>(t.link[ci], G, NONE); c.launches++;
+                } else if (dense_off[chi] >= 0) {
+                    k_link_dense<<<grid_for(c, G), ST, 0, c.stream>>>(
+                        t.F->gkey + (int64_t)ch.sep_cols_parent[0] * G, G, ch.R->kmin[ch.sep_cols[0]],
+                        (uint64_t)dense_range[chi], (const uint32_t *)(scratch + dense_off[chi]), t.link[ci]); c.launches++;
+                } else {
+                    k_link_search<<<grid_for(c, G), ST, 0, c.stream>>>(
+                        key_cols(t, ch.sep_cols_parent), G, key_cols(ch, ch.sep_cols), ch.seg_first,
+                        ch.S_dev, t.link[ci]); c.launches++;
+                }
+                TRY(cudaGetLastError());
             }
+            const bool seg = t.parent >= 0;
             TRY(dalloc(c, &t.w, G));
             TRY(dalloc(c, &t.off, G));
-            k_weights<<<grid_for(c, G), ST, 0, c.stream>>>(t.F->gstart, G, cs, t.w); c.launches++;
-            TRY(cudaGetLastError());
-            if (t.parent >= 0) {
-                uint8_t *heads = nullptr;
-                TRY(dalloc(c, &heads, G));
-                k_seg_heads<<<grid_for(c, G), ST, 0, c.stream>>>(key_cols(t, t.sep_cols), G, heads); c.launches++;
-                TRY(dalloc(c, &t.msg, G));      // S <= G segments
-                TRY(scan_u64_sat(c, t.w, heads, t.off, G, nullptr, t.msg, t.seg_id));
-                dfree(c, heads);
-            } else {
-                TRY(scan_u64_sat(c, t.w, nullptr, t.off, G, total_dev, nullptr, nullptr));
-            }
-        }
-        // downward, root to leaves (preorder)
-        for (int pi = 0; pi < q.k; pi++) {
-            QRel &t = q.r[q.pre[pi]];
-            const int64_t G = t.F->G;
-            const uint64_t *t_down = t.parent >= 0 ? t.down : nullptr;
-            TRY(dalloc(c, &t.mult, G));
-            k_mult<<<grid_for(c, G), ST, 0, c.stream>>>(t.w, t_down, t.seg_id, G, t.mult); c.launches++;
-            if (t.children.empty()) continue;
-            ChildSet cs{};
-            cs.n = (int)t.children.size();
-            std::vector<unsigned long long *> los(cs.n);
-            std::vector<unsigned int *> carries(cs.n);
-            for (int ci = 0; ci < cs.n; ci++) {
-                QRel &ch = q.r[t.children[ci]];
-                const int64_t Sc = std::max<int64_t>(ch.F->G, 1);
-                cs.link[ci] = t.link[ci];
-                cs.msg[ci] = ch.msg;
-                TRY(dalloc(c, &los[ci], Sc));
-                TRY(dalloc(c, &carries[ci], Sc));
-                TRY(cudaMemsetAsync(los[ci], 0, 8 * Sc, c.stream));
-                TRY(cudaMemsetAsync(carries[ci], 0, 4 * Sc, c.stream));
-                cs.lo[ci] = los[ci];
-                cs.carry[ci] = carries[ci];
-            }
-            k_down_contrib<<<grid_for(c, G), ST, 0, c.stream>>>(t.F->gstart, G, t_down, t.seg_id, cs); c.launches++;
-            TRY(cudaGetLastError());
-            for (int ci = 0; ci < cs.n; ci++) {
-                QRel &ch = q.r[t.children[ci]];
-                TRY(dalloc(c, &ch.down, ch.F->G));
-                k_down_finalize<<<grid_for(c, ch.F->G), ST, 0, c.stream>>>(los[ci], carries[ci],
-                                                                         ch.S_dev, ch.down); c.launches++;
-                dfree(c, los[ci]);
-                dfree(c, carries[ci]);
-            }
-        }
-        // live groups (w > 0), the only ones a result row can use
-        for (int i = 0; i < q.k; i++) {
-            QRel &t = q.r[i];
-            const int64_t G = t.F->G;
-            uint8_t *f = nullptr;
-            uint32_t *lidx = nullptr;
-            TRY(dalloc(c, &f, G));
-            TRY(dalloc(c, &lidx, G));
-            TRY(dalloc(c, &t.L_dev, 1));
-            k_nonzero<<<grid_for(c, G), ST, 0, c.stream>>>(t.w, G, f); c.launches++;
-            TRY(scan_u32(c, nullptr, f, lidx, G, t.L_dev));
             TRY(dalloc(c, &t.lgid, G));        // L <= G live groups
             TRY(dalloc(c, &t.loff, G));
             TRY(dalloc(c, &t.lw, G));
-            k_live_compact<<<grid_for(c, G), ST, 0, c.stream>>>(f, lidx, t.w, t.off, G, t.lgid,
-                                                                t.loff, t.lw); c.launches++;
-            if (t.parent >= 0) {
+            TRY(dalloc(c, &t.L_dev, 1));
+            if (seg) {
+                TRY(dalloc(c, &t.msg, G));      // S <= G segments
+                TRY(dalloc(c, &t.seg_id, G));
+                TRY(dalloc(c, &t.seg_first, G + 1));
                 TRY(dalloc(c, &t.lseg_first, G + 1));
-                k_live_segs<<<grid_for(c, G), ST, 0, c.stream>>>(t.seg_first, lidx, t.S_dev,
-                                                                t.L_dev, t.lseg_first); c.launches++;
+                TRY(dalloc(c, &t.S_dev, 1));
             }
+            if (G == 0) {
+                TRY(cudaMemsetAsync(t.L_dev, 0, 4, c.stream));
+                if (seg) {
+                    TRY(cudaMemsetAsync(t.S_dev, 0, 4, c.stream));
+                    TRY(cudaMemsetAsync(t.seg_first, 0, 4, c.stream));
+                    TRY(cudaMemsetAsync(t.lseg_first, 0, 4, c.stream));
+                }
+                continue;
+            }
+            UpSpec u{};
+            u.G = G;
+            u.gstart = t.F->gstart;
+            u.nch = (int)t.children.size();
+            for (int ci = 0; ci < u.nch; ci++) {
+                u.link[ci] = t.link[ci];
+                u.msg[ci] = q.r[t.children[ci]].msg;
+            }
+            u.seg = seg ? 1 : 0;
+            if (seg) u.sep = key_cols(t, t.sep_cols);
+            u.w = t.w;
+            u.off = t.off;
+            u.msg_out = t.msg;
+            u.seg_id = t.seg_id;
+            u.seg_first = t.seg_first;
+            u.S_dev = t.S_dev;
+            u.lgid = t.lgid;
+            u.loff = t.loff;
+            u.lw = t.lw;
+            u.lseg_first = t.lseg_first;
+            u.L_dev = t.L_dev;
+            u.total = seg ? nullptr : total_dev;
+            if (seg && dense_off[ti] >= 0) {
+                u.dense = (uint32_t *)(scratch + dense_off[ti]);
+                u.dense_key = t.F->gkey + (int64_t)t.sep_cols[0] * G;
+                u.dense_mn = t.R->kmin[t.sep_cols[0]];
+            }
+            u.status = (ulonglong2 *)(scratch + st_off[ti] + 16);
+            u.counter = (uint32_t *)(scratch + st_off[ti]);
+            u.err = c.err;
+            k_up_scan<<<(unsigned)ceil_div(G, UP_TILE), ST, UP_SMEM, c.stream>>>(u); c.launches++;
             TRY(cudaGetLastError());
-            dfree(c, f);
-            dfree(c, lidx);
+        }
+        // downward, root to leaves (preorder): mult, each child's down
+        // message, and the relation's own down message finished
+        for (int pi = 0; pi < q.k; pi++) {
+            const int ti = q.pre[pi];
+            QRel &t = q.r[ti];
+            const int64_t G = t.F->G;
+            TRY(dalloc(c, &t.mult, G));
+            if (t.parent >= 0) TRY(dalloc(c, &t.down, G));   // S <= G
+            if (G == 0) continue;
+            DownSpec d{};
+            d.G = G;
+            d.gstart = t.F->gstart;
+            d.w = t.w;
+            d.mult = t.mult;
+            if (t.parent >= 0) {
+                d.has_down = 1;
+                d.self = acc_of(ti);
+                d.seg_id = t.seg_id;
+                d.seg_first = t.seg_first;
+                d.down_out = t.down;
+            }
+            d.nch = (int)t.children.size();
+            for (int ci = 0; ci < d.nch; ci++) {
+                d.link[ci] = t.link[ci];
+                d.msg[ci] = q.r[t.children[ci]].msg;
+                d.acc[ci] = acc_of(t.children[ci]);
+            }
+            launch_down(c, grid_for(c, G), d);
+            TRY(cudaGetLastError());
         }
         // the one synchronisation: |Q| and the device error word
         {
@@ -399,10 +692,10 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             h[0] = 0;
             if (q.r[0].F->G) TRY(cudaMemcpyAsync(h, total_dev, 8, cudaMemcpyDeviceToHost, c.stream));
             TRY(cudaMemcpyAsync(h + 1, c.err, 4, cudaMemcpyDeviceToHost, c.stream));
+            dfree(c, scratch);
             TRY(cudaStreamSynchronize(c.stream));
             q.total = h[0];
             uint32_t err = (uint32_t)(h[1] & 0xffffffffu);
-            dfree(c, total_dev);
             if (err) {
                 cudaMemsetAsync(c.err, 0, 4, c.stream);
                 return (err & ERRF_TIMEOUT) ? GJ_ERR_TIMEOUT : GJ_ERR_CUDA;
@@ -415,6 +708,7 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
     *total_out = q.total;
     return q.overflow ? GJ_ERR_OVERFLOW : GJ_OK;
 fail:
+    dfree(c, scratch);
     return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
 }
 
