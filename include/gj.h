@@ -136,6 +136,32 @@ gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
 gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value);
 
 /*
+ * Failure injection, for tests of the error paths (no counterpart in the
+ * paper).  None of them can hang or fault the device.
+ * GJ_OPT_SPIN_LIMIT: polls after which the bounded wait of the factor
+ * build's group scan (a tile waiting on its predecessors' counts) gives up,
+ * 1 .. 2^22; 0 restores the default (2^22).
+ * GJ_OPT_TEST_STALL: 1 makes the first tile of that scan never publish its
+ * count, so every other tile's wait runs out: the factor build reports
+ * GJ_ERR_TIMEOUT (its results are discarded, every array stays in
+ * bounds), and the context stays usable; 0 turns it off.
+ * GJ_OPT_FAIL_ALLOC_AT: N > 0 makes the N-th device allocation of the
+ * context from now on fail as if the device were out of memory (the call
+ * returns GJ_ERR_OOM and frees what it had allocated); 0 turns it off.
+ */
+#define GJ_OPT_SPIN_LIMIT 3
+#define GJ_OPT_TEST_STALL 4
+#define GJ_OPT_FAIL_ALLOC_AT 5
+
+/*
+ * Device memory the context's pool has handed out and not taken back
+ * (bytes; waits for the context's stream first), and the device
+ * allocations the context has made since GJ_OPT_FAIL_ALLOC_AT was last set
+ * (either pointer may be NULL).  No counterpart in the paper.
+ */
+gj_status gj_pool_usage(gj_ctx *ctx, uint64_t *used_bytes, int64_t *allocations);
+
+/*
  * Profiling (no counterpart in the paper, which reports wall-clock times
  * only).  With out != NULL: synchronises the stream, writes the counters
  * accumulated since the previous read and resets them.  Then turns device
@@ -340,23 +366,27 @@ gj_status gj_summary_load(gj_ctx *ctx, const char *path, gj_query **out);
  * query_off[i+1]), arriving arrival_offsets[i] seconds after the start --
  * and returns when all are answered.  A dispatcher thread releases and
  * plans requests at their arrival times; admission is FIFO while the
- * estimated device memory of the admitted requests stays under hbm_budget;
- * n_slots slot threads, each with its own stream, summarise a request and
- * desummarise its first chunk_rows result rows, so concurrent requests
- * overlap on the device.  results[i] receives |Q|, the status, the first
- * chunk's row count and an order-independent 64-bit hash of its columns,
- * and arrival / admission / summary / first-chunk times (steady clock, s).
- * Relations must be loaded, and their factors should be built, beforehand.
+ * device memory the context's pool has handed out plus the next request's
+ * estimate stays under hbm_budget (a request that cannot fit with nothing
+ * in flight is refused with GJ_ERR_OOM); n_slots slot threads, each with its
+ * own stream, summarise a request and stream its result rows in chunks of
+ * chunk_rows (up to max_rows rows per request, 0 = the whole result)
+ * through the slot's buffers, so concurrent requests overlap on the device.
+ * results[i] receives |Q|, the status, the rows streamed and an
+ * order-independent, position-dependent 64-bit hash of all of them, and
+ * arrival / admission / summary / first-chunk / last-chunk times (steady
+ * clock, s).  Relations must be loaded, and their factors should be built,
+ * beforehand.
  */
 typedef struct gj_server gj_server;
 typedef struct {
     uint64_t total;
     int32_t status;
     int32_t slot;
-    uint64_t chunk_rows;
-    uint64_t chunk_hash;
+    uint64_t rows;                 /* result rows streamed */
+    uint64_t hash;                 /* hash of every streamed row's columns */
     uint64_t est_bytes;
-    double t_arrival, t_admit, t_summary, t_chunk;
+    double t_arrival, t_admit, t_summary, t_chunk, t_last;   /* t_chunk: first chunk out */
 } gj_request_result;
 typedef struct {
     int32_t peak_in_flight;
@@ -364,11 +394,51 @@ typedef struct {
     double wall_s;
 } gj_server_stats;
 gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, uint64_t chunk_rows,
-                           gj_server **out);
+                           uint64_t max_rows, gj_server **out);
 gj_status gj_server_run(gj_server *server, int32_t n_requests, const int32_t *rel_ids,
                         const int32_t *query_off, const double *arrival_offsets,
                         gj_request_result *results, gj_server_stats *stats);
 void gj_server_destroy(gj_server *server);
+
+/*
+ * Row-sharded counting pass: one rank's part, for a query whose relations
+ * are each split by rows across ranks (each rank loads its rows and creates
+ * the query as usual).  No counterpart in the paper's single-machine
+ * setting; it rests on Algorithm 2's sum-out being a sum (Section 3.3): a
+ * message summed over all rows is the sum of the ranks' partial messages,
+ * given the children's global messages.  Every separator must be one
+ * attribute.  Relations are indexed by query position; "children" are a
+ * relation's children in the join tree in position order (the parents are
+ * those of gj_query_sizes).  A message to relation rel's parent is a dense
+ * uint64 vector over rel's separator value domain [lo, lo + len), the same
+ * on every rank; entries saturate at UINT64_MAX like the summary.
+ *
+ * gj_shard_domain: the range [*lo, *hi] of rel's separator attribute over
+ * this rank's rows of rel and of its parent (*lo > *hi when both are
+ * empty); the ranks agree on the union.  rel must not be the root.
+ * gj_shard_up: rel's partial message from this rank's rows, given the
+ * children's global messages (child_msg[c] over [child_lo[c],
+ * child_lo[c] + child_len[c]), device arrays): msg_out[v - lo] (device,
+ * len entries) = sum over rel's local groups with separator value v of
+ * cnt * prod_c child_msg[c][key_c - child_lo[c]].  For the root, lo and
+ * len are ignored and msg_out[0] is the rank's partial join size.
+ * gj_shard_down: given rel's global down message (down_in over [down_lo,
+ * down_lo + down_len); NULL for the root) and the children's global
+ * messages, child_down_out[c] (device, child_len[c] entries) = this rank's
+ * partial down message to child c, and mult_out[g] (device, one entry per
+ * local group in factor order, gj_query_sizes' n_groups[rel]) = the
+ * local groups' partial multiplicities w * down.
+ * All three return GJ_ERR_INVALID for a cyclic query, a separator of
+ * several attributes or missing arrays; up and down wait for their stream.
+ */
+gj_status gj_shard_domain(gj_query *q, int32_t rel, int32_t *lo, int32_t *hi);
+gj_status gj_shard_up(gj_query *q, int32_t rel, const uint64_t *const *child_msg,
+                      const int32_t *child_lo, const int64_t *child_len, uint64_t *msg_out,
+                      int32_t lo, int64_t len);
+gj_status gj_shard_down(gj_query *q, int32_t rel, const uint64_t *down_in, int32_t down_lo,
+                        int64_t down_len, const uint64_t *const *child_msg,
+                        const int32_t *child_lo, const int64_t *child_len,
+                        uint64_t *const *child_down_out, uint64_t *mult_out);
 
 /*
  * Factor construction without any device allocation.  The paper has no

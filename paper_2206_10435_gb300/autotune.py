@@ -1,11 +1,13 @@
-"""Autotuner for the batched summary.
+"""Autotuners for the batched summary and for desummarisation.
 
-The batched path has one tunable that matters on a given GPU and batch
-shape: the size of its persistent grids (SMs x multiplier).  The tuner times
-graph replays of the real batch for each candidate with CUDA events, keeps
-the fastest, and caches the choice in a JSON file keyed by the GPU and a
-coarse signature of the batch (rows, relations, tree depth, key bits), so a
-later batch of the same shape skips the timing.
+The batched path: the size of its persistent grids (SMs x multiplier).  The
+tuner times graph replays of the real batch for each candidate with CUDA
+events, keeps the fastest, and caches the choice in a JSON file keyed by the
+GPU and a coarse signature of the batch (rows, relations, tree depth, key
+bits), so a later batch of the same shape skips the timing.
+
+Desummarisation: the emit kernel's rows per thread, timed on a real window
+of the query and cached by the GPU and the result's shape (tune_emit).
 """
 from __future__ import annotations
 
@@ -52,6 +54,73 @@ def tune_batch(batch, candidates=CANDIDATES, reps: int = 3, cache_path: str = DE
     best = min(times, key=times.get)
     batch.set_grid_mult(best)
     entry = {"grid_mult": best, "ms": times[best], "candidates_ms": {str(k): v for k, v in times.items()}}
+    if use_cache:
+        cache[key] = entry
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + f".{os.getpid()}.tmp"
+        json.dump(cache, open(tmp, "w"), indent=1)
+        os.replace(tmp, cache_path)
+    return dict(entry, cached=False)
+
+
+# ---------------------------------------------------------------- emit
+# The desummarise emit kernel writes RPT consecutive rows per thread (2, 4 or
+# 8): more rows per thread mean fewer block lookups per row, fewer mean more
+# threads in flight.  Which is faster depends on the GPU and on the result's
+# shape (relations, and how many rows a key path's block holds), so the
+# tuner times one real window per choice and caches the best.
+EMIT_RPT = (2, 4, 8)
+
+
+def emit_signature(query, gpu_name: str, window: int) -> str:
+    rows_per_block = 0
+    try:
+        groups = max(1, min(query.n_groups))
+        rows_per_block = int(round(math.log2(max(1, (query.total or 1) / groups))))
+    except (TypeError, ValueError):
+        pass
+    return f"{gpu_name}|emit|rel{query.n_rel}|cols{len(query.col_width)}|rpb2^{rows_per_block}|win2^{int(math.log2(window))}"
+
+
+def tune_emit(ctx, query, window: int = 1 << 24, reps: int = 3, cache_path: str = DEFAULT_CACHE,
+              use_cache: bool = True) -> dict:
+    """Times gj_desummarize of the query's first `window` rows for every
+    rows-per-thread choice; leaves the fastest set on the context (the
+    option is read at each launch) and returns it with the timings."""
+    import torch
+    from . import gj
+    gpu = torch.cuda.get_device_name(ctx.device)
+    total = query.total
+    if not total:
+        return {"rpt": 4, "skipped": "empty result"}
+    n = min(window, total)
+    key = emit_signature(query, gpu, n)
+    cache = {}
+    if use_cache and os.path.exists(cache_path):
+        try:
+            cache = json.load(open(cache_path))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, int(cache[key]["rpt"]))
+        return dict(cache[key], cached=True)
+    out = query.alloc_columns(n)
+    stream = ctx.stream
+    times = {}
+    for rpt in EMIT_RPT:
+        ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, rpt)
+        query.desummarize(0, n, out=out)      # warm-up
+        stream.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            query.desummarize(0, n, out=out)
+        t1.record(stream)
+        t1.synchronize()
+        times[rpt] = t0.elapsed_time(t1) / reps
+    best = min(times, key=times.get)
+    ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, best)
+    entry = {"rpt": best, "ms": times[best], "candidates_ms": {str(k): v for k, v in times.items()}}
     if use_cache:
         cache[key] = entry
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)

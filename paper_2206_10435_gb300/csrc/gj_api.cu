@@ -202,7 +202,43 @@ gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value) {
         ctx->s.c.tri_mode = (int)value;
         return GJ_OK;
     }
+    if (option == GJ_OPT_SPIN_LIMIT) {
+        if (value < 0 || value > (int64_t)SPIN_LIMIT) return GJ_ERR_INVALID;
+        ctx->s.c.spin_limit = value == 0 ? SPIN_LIMIT : (uint32_t)value;
+        return GJ_OK;
+    }
+    if (option == GJ_OPT_TEST_STALL) {
+        if (value < 0 || value > 1) return GJ_ERR_INVALID;
+        ctx->s.c.test_stall = value != 0;
+        return GJ_OK;
+    }
+    if (option == GJ_OPT_FAIL_ALLOC_AT) {
+        if (value < 0) return GJ_ERR_INVALID;
+        ctx->s.c.fail_alloc_at = value;
+        ctx->s.c.allocs = 0;
+        return GJ_OK;
+    }
     return GJ_ERR_INVALID;
+}
+
+gj_status gj_pool_usage(gj_ctx *ctx, uint64_t *used_bytes, int64_t *allocations) {
+    if (!ctx) return GJ_ERR_INVALID;
+    DeviceGuard g(ctx->s.c.device);
+    Ctx &c = ctx->s.c;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) { cudaGetLastError(); return GJ_ERR_CUDA; }
+    if (used_bytes) {
+        *used_bytes = 0;
+        if (c.pool) {
+            size_t v = 0;   // the attribute is a 64-bit value
+            if (cudaMemPoolGetAttribute(c.pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) {
+                cudaGetLastError();
+                return GJ_ERR_CUDA;
+            }
+            *used_bytes = (uint64_t)v;
+        }
+    }
+    if (allocations) *allocations = c.allocs;
+    return GJ_OK;
 }
 
 gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream) {

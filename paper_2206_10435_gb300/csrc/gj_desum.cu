@@ -170,6 +170,11 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
                const uint32_t *__restrict__ lo_in, const uint64_t *__restrict__ unit_in,
                ExpandOut o) {
     __shared__ uint32_t s_off[EXP_TILE + 1];
+    // the tile's items, staged by coalesced loads: first row, rows per way,
+    // first live group in the segment, product of the counts so far
+    __shared__ uint64_t s_iA[EXP_TILE + 1];
+    __shared__ uint64_t s_iu[EXP_TILE + 1];
+    __shared__ uint32_t s_ilo[EXP_TILE + 1];
     __shared__ uint64_t s_A[EXP_TILE];   // tile map only: first rows of the tile's blocks
     __shared__ uint64_t s_end;            // and the end of its last block
     const int64_t F = *F_dev, Fout = *Fout_dev;
@@ -187,16 +192,21 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             return;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nitems; t += DT) s_off[t] = excl[first + t];
+        for (int t = threadIdx.x; t < nitems; t += DT) {
+            s_off[t] = excl[first + t];
+            s_iA[t] = s.A[first + t];
+            s_iu[t] = unit_in[first + t];
+            s_ilo[t] = lo_in[first + t];
+        }
         __syncthreads();
         for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
             int a = 0, b = nitems;   // last t with s_off[t] <= slot
             while (a < b) { int m = (a + b) >> 1; if (s_off[m] <= (uint32_t)slot) a = m + 1; else b = m; }
             const int64_t i = first + a - 1;
-            const uint32_t h = lo_in[i] + (uint32_t)(slot - s_off[a - 1]);
+            const uint32_t h = s_ilo[a - 1] + (uint32_t)(slot - s_off[a - 1]);
             const uint32_t g = s.lgid[h];
-            const uint64_t unit = unit_in[i];
-            const uint64_t A = s.A[i] + unit * s.loff[h];
+            const uint64_t unit = s_iu[a - 1];
+            const uint64_t A = s_iA[a - 1] + unit * s.loff[h];
             o.A[slot] = A;
             if (o.W) o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
             if (o.tile_first) {
@@ -294,6 +304,16 @@ int child_index(const QRel &parent, int child_pos) {
     return -1;
 }
 
+// Frees a frontier when the scope ends, unless it was handed on.
+struct FrontierHold {
+    Ctx &c;
+    Frontier &f;
+    bool held = true;
+    ~FrontierHold() {
+        if (held) frontier_free(c, f);
+    }
+};
+
 cudaError_t frontier_alloc(Ctx &c, Frontier &f, int64_t cap, int depth, bool keep_last,
                            bool need_w = true) {
     f.cap = cap;
@@ -326,9 +346,12 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
     const QRel &root = q.r[q.pre[0]];
     const int64_t cap = (int64_t)(row_end - row0);
     const int pgrid = std::max(1, std::min<int>((int)ceil_div(cap, EXP_TILE), c.num_sms * 8));
+    // every array is freed on the way out of an error
+    Temps tmp(c);
     uint32_t *rr = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &rr, 2));
+    GJ_CUDA_TRY(tmp.alloc(&rr, 2));
     Frontier cur;
+    FrontierHold hold_cur{c, cur};
     GJ_CUDA_TRY(frontier_alloc(c, cur, cap, 1, keep_last && depth == 1));
     k_root_range<<<1, 1, 0, c.stream>>>(root.loff, root.lw, root.L_dev, row0, row_end, rr,
                                         cur.F_dev); c.launches++;
@@ -336,7 +359,7 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
                                                       root.F->gstart, cur.A, cur.W, cur.grp[0],
                                                       cur.lh, cur.unit); c.launches++;
     GJ_CUDA_TRY(cudaGetLastError());
-    dfree(c, rr);
+    tmp.free(rr);
     for (int j = 1; j < depth; j++) {
         const int tpos = q.pre[j];
         const QRel &t = q.r[tpos];
@@ -364,15 +387,17 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         s.A = cur.A;
         s.W = cur.W;
         for (int p = 0; p < j; p++) s.grp[p] = cur.grp[p];
+        Temps lt(c);   // this level's temporaries
         uint32_t *cnt = nullptr, *lo = nullptr, *excl = nullptr, *slot_first = nullptr;
         uint64_t *unit = nullptr;
-        GJ_CUDA_TRY(dalloc(c, &cnt, cap));
-        GJ_CUDA_TRY(dalloc(c, &lo, cap));
-        GJ_CUDA_TRY(dalloc(c, &unit, cap));
-        GJ_CUDA_TRY(dalloc(c, &excl, cap));
-        GJ_CUDA_TRY(dalloc(c, &slot_first, ceil_div(cap, EXP_TILE) + 1));
+        GJ_CUDA_TRY(lt.alloc(&cnt, cap));
+        GJ_CUDA_TRY(lt.alloc(&lo, cap));
+        GJ_CUDA_TRY(lt.alloc(&unit, cap));
+        GJ_CUDA_TRY(lt.alloc(&excl, cap));
+        GJ_CUDA_TRY(lt.alloc(&slot_first, ceil_div(cap, EXP_TILE) + 1));
         const bool last = (j == depth - 1);
         Frontier nxt;
+        FrontierHold hold_nxt{c, nxt};
         // the last frontier's W (counts of the chosen groups) is not used
         GJ_CUDA_TRY(frontier_alloc(c, nxt, cap, j + 1, last && keep_last, !last));
         k_expand_count<<<grid_for(c, cap), DT, 0, c.stream>>>(s, cur.F_dev, row0, row_end, cnt, lo,
@@ -396,15 +421,12 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
         k_expand_write<<<pgrid, DT, 0, c.stream>>>(s, cur.F_dev, excl, nxt.F_dev, slot_first, lo,
                                                    unit, o); c.launches++;
         GJ_CUDA_TRY(cudaGetLastError());
-        dfree(c, cnt);
-        dfree(c, lo);
-        dfree(c, unit);
-        dfree(c, excl);
-        dfree(c, slot_first);
         frontier_free(c, cur);
-        cur = nxt;
+        cur = nxt;               // held by hold_cur from here on
+        hold_nxt.held = false;
     }
     out = cur;
+    hold_cur.held = false;
     return cudaSuccess;
 }
 
@@ -624,7 +646,10 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
     }
     cudaError_t e = expand(q, row0, row0 + n, q.k, false, f, tm.tile_first ? &tm : nullptr);
     if (c.prof) cudaEventRecord(c.event(true), c.stream);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+    if (e != cudaSuccess) {
+        dfree(c, tm.tile_first);
+        return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+    }
     uint64_t width = 0;
     for (int v = 0; v < (int)q.var_rel.size(); v++) width += 4;
     for (size_t p = 0; p < q.col_rel.size(); p++) width += q.r[q.col_rel[p]].R->pw[q.col_pay[p]];
@@ -673,7 +698,7 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
     }
     frontier_free(c, f);
     dfree(c, tm.tile_first);
-    if (e != cudaSuccess) return GJ_ERR_CUDA;
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
     gj_status st = check_device_error(c);
     if (st != GJ_OK) return st;
     *n_out = n;

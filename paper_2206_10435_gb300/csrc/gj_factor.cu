@@ -45,8 +45,16 @@ __global__ void k_minmax(ColSet cs, int64_t n, int32_t *mm) {
     int c = blockIdx.y;
     const int32_t *col = cs.col[c];
     int32_t lo = INT32_MAX, hi = INT32_MIN;
-    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT) {
-        int32_t v = col[i];
+    const int64_t stride = (int64_t)gridDim.x * FT;
+    int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {   // four loads in flight
+        const int32_t v0 = __ldg(col + i), v1 = __ldg(col + i + stride);
+        const int32_t v2 = __ldg(col + i + 2 * stride), v3 = __ldg(col + i + 3 * stride);
+        lo = min(lo, min(min(v0, v1), min(v2, v3)));
+        hi = max(hi, max(max(v0, v1), max(v2, v3)));
+    }
+    for (; i < n; i += stride) {
+        const int32_t v = __ldg(col + i);
         lo = min(lo, v);
         hi = max(hi, v);
     }
@@ -224,7 +232,8 @@ cudaError_t relation_minmax(Ctx &c, Relation &R) {
     R.kmax.assign(R.nk, 0);
     if (R.n > 0) {
         int32_t *mm = nullptr;
-        GJ_CUDA_TRY(dalloc(c, &mm, 2 * R.nk));
+        Temps tmp(c);
+        GJ_CUDA_TRY(tmp.alloc(&mm, 2 * R.nk));
         ColSet cs{};
         cs.ncol = R.nk;
         for (int i = 0; i < R.nk; i++) cs.col[i] = R.key[i];
@@ -237,7 +246,6 @@ cudaError_t relation_minmax(Ctx &c, Relation &R) {
         GJ_CUDA_TRY(cudaMemcpyAsync(h, mm, sizeof(int32_t) * 2 * R.nk, cudaMemcpyDeviceToHost, c.stream));
         GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
         for (int i = 0; i < R.nk; i++) { R.kmin[i] = h[2 * i]; R.kmax[i] = h[2 * i + 1]; }
-        dfree(c, mm);
     }
     R.have_minmax = true;
     return cudaSuccess;
@@ -283,6 +291,8 @@ struct GroupScanSpec {
     unsigned long long *status;   // lookback state, one word per tile
     uint32_t *counter;            // tile counter
     uint32_t *err;
+    uint32_t spin_limit;          // polls of a bounded wait
+    int stall;                    // failure injection: tile 0 never publishes
 };
 
 // shared-memory slot of word q (q = 0 is the previous tile's last word): one
@@ -292,7 +302,7 @@ __device__ __forceinline__ int gs_slot(int q) { return q + (q >> 4); }
 constexpr int GS_SLOTS = GS_TILE + 1 + (GS_TILE + 1) / 16 + 1;
 
 template <int MODE>
-__global__ void __launch_bounds__(GS_THREADS)
+__global__ void __launch_bounds__(GS_THREADS, 4)
 k_group_scan(GroupScanSpec s, int64_t n) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_lo = (uint64_t *)smem;
@@ -363,40 +373,14 @@ k_group_scan(GroupScanSpec s, int64_t n) {
         agg += v;
     }
     const uint32_t excl = before + x - cnt;
-    if (warp == GS_THREADS / 32 - 1) {
-        const uint32_t carry = warp_lookback<uint32_t, AddU32>(s.status, tile, agg, lane, s.err);
-        if (lane == 0) {
-            s_carry = carry;
-            if (base + GS_TILE >= n) {   // the last tile: the group count
-                *s.gcount = carry + agg;
-                s.gstart[carry + agg] = (uint32_t)n;
-            }
-        }
-    }
-    __syncthreads();
-    // group starts and keys
-    uint32_t g = s_carry + excl;
+    // the tile's aggregate goes out first; the row order and the payloads do
+    // not depend on the group numbering, so they are gathered while the
+    // lookback waits on the predecessors
+    // (published by the lane that later publishes the prefix: program order
+    // keeps the prefix last)
+    const bool silent = s.stall && tile == 0;
+    if (warp == GS_THREADS / 32 - 1 && lane == 0 && !silent) publish_aggregate<uint32_t>(s.status, tile, agg);
     const uint64_t rmask = s.row_bits ? ((1ull << s.row_bits) - 1) : 0ull;
-    while (hmask) {
-        const int i = __ffs(hmask) - 1;
-        hmask &= hmask - 1;
-        const int e = tid * GS_ITEMS + i;
-        const int64_t idx = base + e;
-        s.gstart[g] = (uint32_t)idx;
-        const uint64_t klo = s_lo[gs_slot(e + 1)], khi = MODE == 2 ? s_hi[gs_slot(e + 1)] : 0ull;
-        for (int c = 0; c < s.u.ncol; c++) {
-            const uint64_t k = s.u.hi[c] ? khi : klo;
-            const uint64_t mask = s.u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << s.u.bits[c]) - 1);
-            const uint32_t v = (s.u.shift[c] < 64 ? (uint32_t)((k >> s.u.shift[c]) & mask) : 0u) + (uint32_t)s.u.mn[c];
-            s.gkey[(int64_t)s.u.col[c] * s.gkey_stride + g] = (int32_t)v;
-        }
-        if (s.u.nother) {
-            const uint32_t r = MODE == 0 ? (uint32_t)(klo & rmask) : s.perm_in[idx];
-            for (int c = 0; c < s.u.nother; c++)
-                s.gkey[(int64_t)s.u.other_col[c] * s.gkey_stride + g] = s.u.other[c][r];
-        }
-        g++;
-    }
     // row order and payloads in group order, coalesced; each thread issues
     // its 16 gathers of a payload column together
     uint32_t r[GS_ITEMS];
@@ -434,6 +418,171 @@ k_group_scan(GroupScanSpec s, int64_t n) {
                 if (i * GS_THREADS + tid < tile_n) dst[base + i * GS_THREADS + tid] = v[i];
         }
     }
+    if (warp == GS_THREADS / 32 - 1) {
+        const uint32_t carry = warp_lookback_published<uint32_t, AddU32>(s.status, tile, agg, lane, s.err,
+                                                                          s.spin_limit);
+        if (lane == 0) {
+            s_carry = carry;
+            if (base + GS_TILE >= n) {   // the last tile: the group count
+                *s.gcount = carry + agg;
+                s.gstart[carry + agg] = (uint32_t)n;
+            }
+        }
+    }
+    __syncthreads();
+    // group starts and keys
+    uint32_t g = s_carry + excl;
+    while (hmask) {
+        const int i = __ffs(hmask) - 1;
+        hmask &= hmask - 1;
+        const int e = tid * GS_ITEMS + i;
+        const int64_t idx = base + e;
+        s.gstart[g] = (uint32_t)idx;
+        const uint64_t klo = s_lo[gs_slot(e + 1)], khi = MODE == 2 ? s_hi[gs_slot(e + 1)] : 0ull;
+        for (int c = 0; c < s.u.ncol; c++) {
+            const uint64_t k = s.u.hi[c] ? khi : klo;
+            const uint64_t mask = s.u.bits[c] >= 32 ? 0xFFFFFFFFull : ((1ull << s.u.bits[c]) - 1);
+            const uint32_t v = (s.u.shift[c] < 64 ? (uint32_t)((k >> s.u.shift[c]) & mask) : 0u) + (uint32_t)s.u.mn[c];
+            s.gkey[(int64_t)s.u.col[c] * s.gkey_stride + g] = (int32_t)v;
+        }
+        if (s.u.nother) {
+            const uint32_t r = MODE == 0 ? (uint32_t)(klo & rmask) : s.perm_in[idx];
+            for (int c = 0; c < s.u.nother; c++)
+                s.gkey[(int64_t)s.u.other_col[c] * s.gkey_stride + g] = s.u.other[c][r];
+        }
+        g++;
+    }
+}
+
+// ------------------------------------------------------------ run sort
+// A key that needs more than one word together with the row id: the rows
+// are first sorted by the leading columns with the row id under them
+// (keys-only), then every run of rows with equal leading columns is sorted
+// by the remaining columns and the row id, by one warp in registers: a
+// bitonic network over 32 * E elements (element e = k * 32 + lane, padding
+// past the run sorts last).  Runs longer than RUN_MAX are not sorted here;
+// a flag tells the host to build that factor the two-word way instead.
+constexpr int RUN_MAX = 256;
+
+struct RunSortSpec {
+    const uint64_t *a;            // lead << row_bits | row, sorted
+    int row_bits;
+    const uint32_t *run_start;    // [R + 1]
+    const uint32_t *R_dev;        // number of runs
+    PackSrc rest;                 // the remaining columns, packed from bit 0
+    uint64_t *hi;                 // out: the leading columns' word
+    uint64_t *lo;                 // out: the remaining columns' word
+    uint32_t *perm;               // out: row ids
+    uint32_t *too_long;           // set when a run exceeds RUN_MAX
+};
+
+__device__ __forceinline__ bool kr_greater(uint64_t ka, uint32_t ra, uint64_t kb, uint32_t rb) {
+    return ka > kb || (ka == kb && ra > rb);
+}
+
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&key)[E], uint32_t (&row)[E], int lane) {
+    constexpr int N = 32 * E;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                // partners in the same lane: exchange in registers
+                const int ks = stride >> 5;
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    const int kp = k ^ ks;
+                    if (kp > k) {
+                        const bool up = ((k * 32 + lane) & size) == 0;
+                        if (kr_greater(key[k], row[k], key[kp], row[kp]) == up) {
+                            const uint64_t tk = key[k]; key[k] = key[kp]; key[kp] = tk;
+                            const uint32_t tr = row[k]; row[k] = row[kp]; row[kp] = tr;
+                        }
+                    }
+                }
+            } else {
+                // partners in another lane: exchange by shuffle; the lane of
+                // the lower element keeps the smaller one on an ascending run
+#pragma unroll
+                for (int k = 0; k < E; k++) {
+                    const uint64_t ok = __shfl_xor_sync(0xffffffffu, key[k], stride);
+                    const uint32_t orow = __shfl_xor_sync(0xffffffffu, row[k], stride);
+                    const bool up = ((k * 32 + lane) & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    const bool gt = kr_greater(key[k], row[k], ok, orow);
+                    if ((lower == up) ? gt : !gt) { key[k] = ok; row[k] = orow; }
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void sort_run(const RunSortSpec &s, uint32_t p0, uint32_t m, int lane) {
+    const uint64_t rmask = (1ull << s.row_bits) - 1;
+    uint64_t key[E];
+    uint32_t row[E];
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const uint32_t e = k * 32 + lane;
+        row[k] = e < m ? (uint32_t)(__ldg((const unsigned long long *)s.a + p0 + e) & rmask) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int k = 0; k < E; k++) key[k] = row[k] != 0xffffffffu ? pack_word(s.rest, row[k]) : ~0ull;
+    warp_bitonic<E>(key, row, lane);
+    const uint64_t lead = __ldg((const unsigned long long *)s.a + p0) >> s.row_bits;
+#pragma unroll
+    for (int k = 0; k < E; k++) {
+        const uint32_t e = k * 32 + lane;
+        if (e < m) {
+            s.hi[p0 + e] = lead;
+            s.lo[p0 + e] = key[k];
+            s.perm[p0 + e] = row[k];
+        }
+    }
+}
+
+// one warp per run, runs taken in turn
+__global__ void __launch_bounds__(256) k_sort_runs(RunSortSpec s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nruns = *s.R_dev;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nruns; r += warps) {
+        const uint32_t p0 = s.run_start[r];
+        const uint32_t m = s.run_start[r + 1] - p0;
+        if (m <= 32) sort_run<1>(s, p0, m, lane);
+        else if (m <= 64) sort_run<2>(s, p0, m, lane);
+        else if (m <= 128) sort_run<4>(s, p0, m, lane);
+        else if (m <= RUN_MAX) sort_run<8>(s, p0, m, lane);
+        else {
+            // too long for the registers: flag it (the host builds this
+            // factor another way) and leave valid row ids behind, so that the
+            // group scan that follows reads only rows of the relation
+            if (lane == 0) atomicOr(s.too_long, 1u);
+            const uint64_t rmask = (1ull << s.row_bits) - 1;
+            for (uint32_t e = lane; e < m; e += 32) {
+                const uint64_t w = s.a[p0 + e];
+                s.hi[p0 + e] = w >> s.row_bits;
+                s.lo[p0 + e] = 0ull;
+                s.perm[p0 + e] = (uint32_t)(w & rmask);
+            }
+        }
+    }
+}
+
+// run heads of the sorted words: the leading columns differ from the
+// previous row's
+__global__ void k_run_heads(const uint64_t *__restrict__ a, int row_bits, int64_t n, uint8_t *head) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        head[i] = i == 0 || (a[i] >> row_bits) != (a[i - 1] >> row_bits);
+}
+
+__global__ void k_run_starts(const uint8_t *__restrict__ head, const uint32_t *__restrict__ excl, int64_t n,
+                             const uint32_t *R_dev, uint32_t *run_start) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        if (head[i]) run_start[excl[i]] = (uint32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) run_start[*R_dev] = (uint32_t)n;
 }
 
 // One factor build in two stages, so that the builds of several relations
@@ -451,6 +600,9 @@ struct FactorBuild {
     uint32_t *gstart = nullptr;    // [n+1]
     int32_t *gkey_n = nullptr;     // [nk*n]
     uint32_t *gcount = nullptr;
+    // wide keys sorted by their leading columns, then run by run
+    bool force_two = false;        // build the two-word way (a run was too long)
+    uint32_t *too_long = nullptr;
     // keys of more than two words
     uint8_t *head = nullptr;
     uint32_t *gid = nullptr;
@@ -458,6 +610,7 @@ struct FactorBuild {
 };
 
 void fb_free(Ctx &c, FactorBuild &b) {
+    dfree(c, b.too_long);
     dfree(c, b.gstart);
     dfree(c, b.gkey_n);
     dfree(c, b.gcount);
@@ -513,17 +666,29 @@ template <int MODE>
 cudaError_t launch_group_scan(Ctx &c, GroupScanSpec &gs, int64_t n) {
     const int64_t tiles = ceil_div(n, GS_TILE);
     unsigned long long *state = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &state, tiles + 2));
+    Temps tmp(c);
+    GJ_CUDA_TRY(tmp.alloc(&state, tiles + 2));
     GJ_CUDA_TRY(cudaMemsetAsync(state, 0, 8 * (tiles + 2), c.stream));
     gs.counter = (uint32_t *)state;
     gs.status = state + 2;
     gs.err = c.err;
+    gs.spin_limit = c.spin_limit;
+    gs.stall = c.test_stall ? 1 : 0;
     const size_t smem = (size_t)GS_SLOTS * 8 * (MODE == 2 ? 2 : 1);
     GJ_CUDA_TRY(cudaFuncSetAttribute(k_group_scan<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_group_scan<MODE><<<(unsigned)tiles, GS_THREADS, smem, c.stream>>>(gs, n); c.launches++;
-    cudaError_t e = cudaGetLastError();
-    dfree(c, state);
-    return e;
+    return cudaGetLastError();
+}
+
+// The leading columns of `order` that fit one word with the row id, when
+// the remaining ones fit another: their number, else 0.
+int run_split(const std::vector<int> &order, const std::vector<int> &bits, int row_bits) {
+    int nlead = 0, used = row_bits;
+    while (nlead < (int)order.size() && used + bits[order[nlead]] <= 64) used += bits[order[nlead++]];
+    if (nlead == 0 || nlead == (int)order.size()) return 0;
+    int rest = 0;
+    for (size_t i = nlead; i < order.size(); i++) rest += bits[order[i]];
+    return rest <= 64 ? nlead : 0;
 }
 
 // stage 1 (key ranges known): rows sorted by the key tuple; keys of one or
@@ -585,9 +750,11 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
         gs.gkey = b.gkey_n;
         gs.gkey_stride = n;
         gs.gcount = b.gcount;
+        // temporaries of this build, freed on every way out
+        Temps tmp(c);
         uint64_t *k1 = nullptr, *k2 = nullptr, *kres = nullptr;
-        GJ_CUDA_TRY(dalloc(c, &k1, n));
-        GJ_CUDA_TRY(dalloc(c, &k2, n));
+        GJ_CUDA_TRY(tmp.alloc(&k1, n));
+        GJ_CUDA_TRY(tmp.alloc(&k2, n));
         if (words.size() == 1 && kbits + row_bits <= 64) {
             // MODE 0: the row id rides under the key; a keys-only sort of the
             // key bits
@@ -602,24 +769,74 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
         } else if (words.size() == 1) {
             // MODE 1: (key, row id) pairs
             uint32_t *v1 = nullptr, *v2 = nullptr, *vres = nullptr;
-            GJ_CUDA_TRY(dalloc(c, &v1, n));
-            GJ_CUDA_TRY(dalloc(c, &v2, n));
+            GJ_CUDA_TRY(tmp.alloc(&v1, n));
+            GJ_CUDA_TRY(tmp.alloc(&v2, n));
             PackSrc ps = pack_src(R, words[0], bits, 0);
             GJ_CUDA_TRY(radix_sort_words(c, &ps, k1, k2, v1, v2, n, 0, kbits, &kres, &vres));
             // the sorted row ids become the factor's row order
             F.perm = vres;
-            if (vres == v1) dfree(c, v2); else dfree(c, v1);
+            tmp.keep(vres);
             gs.lo = kres;
             gs.perm_in = F.perm;
             gs.u = unpack_spec(R, order, words, bits, 0);
             GJ_CUDA_TRY(launch_group_scan<1>(c, gs, n));
+        } else if (int nlead = run_split(order, bits, row_bits); !b.force_two && nlead > 0) {
+            // the leading columns with the row id under them (keys-only),
+            // then each run of equal leading columns sorted by the rest in
+            // registers; the group scan then reads (lead, rest) words
+            std::vector<int> lead(order.begin(), order.begin() + nlead);
+            std::vector<int> rest(order.begin() + nlead, order.end());
+            std::reverse(lead.begin(), lead.end());   // least significant first
+            std::reverse(rest.begin(), rest.end());
+            int lead_bits = 0;
+            for (int col : lead) lead_bits += bits[col];
+            PackSrc pa = pack_src(R, lead, bits, row_bits);
+            GJ_CUDA_TRY(radix_sort_words(c, &pa, k1, k2, nullptr, nullptr, n, row_bits, lead_bits, &kres, nullptr));
+            uint8_t *head = nullptr;
+            uint32_t *excl = nullptr, *run_start = nullptr, *R_dev = nullptr;
+            GJ_CUDA_TRY(tmp.alloc(&head, n));
+            GJ_CUDA_TRY(tmp.alloc(&excl, n));
+            GJ_CUDA_TRY(tmp.alloc(&run_start, n + 1));
+            GJ_CUDA_TRY(tmp.alloc(&R_dev, 1));
+            k_run_heads<<<grid_for(c, n), FT, 0, c.stream>>>(kres, row_bits, n, head); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            GJ_CUDA_TRY(scan_u32(c, nullptr, head, excl, n, R_dev));
+            k_run_starts<<<grid_for(c, n), FT, 0, c.stream>>>(head, excl, n, R_dev, run_start); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            uint64_t *hiw = nullptr;
+            GJ_CUDA_TRY(tmp.alloc(&hiw, n));
+            GJ_CUDA_TRY(dalloc(c, &F.perm, n));
+            GJ_CUDA_TRY(dalloc(c, &b.too_long, 1));
+            GJ_CUDA_TRY(cudaMemsetAsync(b.too_long, 0, 4, c.stream));
+            uint64_t *low = kres == k1 ? k2 : k1;
+            RunSortSpec rs{};
+            rs.a = kres;
+            rs.row_bits = row_bits;
+            rs.run_start = run_start;
+            rs.R_dev = R_dev;
+            rs.rest = pack_src(R, rest, bits, 0);
+            rs.hi = hiw;
+            rs.lo = low;
+            rs.perm = F.perm;
+            rs.too_long = b.too_long;
+            k_sort_runs<<<c.num_sms * 8, 256, 0, c.stream>>>(rs); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            tmp.free(head);
+            tmp.free(excl);
+            tmp.free(run_start);
+            tmp.free(R_dev);
+            gs.lo = low;
+            gs.hi = hiw;
+            gs.perm_in = F.perm;
+            gs.u = unpack_spec(R, order, {rest, lead}, bits, 0);
+            GJ_CUDA_TRY(launch_group_scan<2>(c, gs, n));
         } else {
             // MODE 2: the low word sorts with row ids; the high word sorts
             // carrying positions in the low word's order, and one gather then
             // brings the row ids and the low word into the final order
             uint32_t *v1 = nullptr, *v2 = nullptr, *perm0 = nullptr;
-            GJ_CUDA_TRY(dalloc(c, &v1, n));
-            GJ_CUDA_TRY(dalloc(c, &v2, n));
+            GJ_CUDA_TRY(tmp.alloc(&v1, n));
+            GJ_CUDA_TRY(tmp.alloc(&v2, n));
             PackSrc ps = pack_src(R, words[0], bits, 0);
             int lo_bits = 0;
             for (int col : words[0]) lo_bits += bits[col];
@@ -639,8 +856,8 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             }
             uint64_t *h1 = nullptr, *hres = nullptr;
             uint32_t *pos2 = nullptr, *pres = nullptr;
-            GJ_CUDA_TRY(dalloc(c, &h1, n));
-            GJ_CUDA_TRY(dalloc(c, &pos2, n));
+            GJ_CUDA_TRY(tmp.alloc(&h1, n));
+            GJ_CUDA_TRY(tmp.alloc(&pos2, n));
             k_pack_pos<<<grid_for(c, n), FT, 0, c.stream>>>(ph, perm0, n, kfree, vfree); c.launches++;
             GJ_CUDA_TRY(cudaGetLastError());
             GJ_CUDA_TRY(radix_sort_words(c, nullptr, kfree, h1, vfree, pos2, n, 0, shift, &hres, &pres));
@@ -649,21 +866,13 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             k_compose<<<grid_for(c, n), FT, 0, c.stream>>>(pres, perm0, lo_sorted, n, perm, lo_final); c.launches++;
             GJ_CUDA_TRY(cudaGetLastError());
             F.perm = perm;
-            // free everything but perm, hres and lo_final
-            for (uint32_t *v : {v1, v2, pos2})
-                if (v != perm) dfree(c, v);
-            for (uint64_t *k : {k1, k2, h1})
-                if (k != hres && k != lo_final) dfree(c, k);
-            k1 = hres;
-            k2 = lo_final;
+            tmp.keep(perm);
             gs.lo = lo_final;
             gs.hi = hres;
             gs.perm_in = F.perm;
             gs.u = unpack_spec(R, order, words, bits, 0);
             GJ_CUDA_TRY(launch_group_scan<2>(c, gs, n));
         }
-        dfree(c, k1);
-        dfree(c, k2);
         return cudaSuccess;
     }
     // keys of three or more words: (word, row id) sorts word by word, then
@@ -671,7 +880,8 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
     // found with sequential reads
     GJ_CUDA_TRY(dalloc(c, &F.perm, n));
     uint64_t *keys = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &keys, n));
+    Temps tmp(c);
+    GJ_CUDA_TRY(tmp.alloc(&keys, n));
     for (size_t w = 0; w < words.size(); w++) {   // least significant word first
         const std::vector<int> &wcols = words[w];
         PackSpec ps{};
@@ -688,7 +898,7 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
         GJ_CUDA_TRY(cudaGetLastError());
         GJ_CUDA_TRY(radix_sort_u64_u32(c, keys, F.perm, n, shift));
     }
-    dfree(c, keys);
+    tmp.free(keys);
     GJ_CUDA_TRY(dalloc(c, &b.head, n));
     GJ_CUDA_TRY(dalloc(c, &b.gid, n));
     GJ_CUDA_TRY(dalloc(c, &b.gcount, 1));
@@ -773,10 +983,11 @@ cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const st
         if (!r->have_minmax && std::find(need.begin(), need.end(), r) == need.end()) need.push_back(r);
     size_t words_mm = 0;
     for (Relation *r : need) words_mm += 2 * r->nk;
-    if (words_mm * 4 > (1 << 16) || m * 4 > (1 << 16)) return cudaErrorInvalidValue;
+    if (words_mm * 4 > (1 << 16) || m * 8 > (1 << 16)) return cudaErrorInvalidValue;
     if (words_mm) {
         int32_t *mm = nullptr;
-        GJ_CUDA_TRY(dalloc(c, &mm, words_mm));
+        Temps tmp(c);
+        GJ_CUDA_TRY(tmp.alloc(&mm, words_mm));
         size_t off = 0;
         for (Relation *r : need) {
             if (r->n > 0) {
@@ -803,7 +1014,6 @@ cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const st
             r->have_minmax = true;
             off += 2 * r->nk;
         }
-        dfree(c, mm);
     }
     std::vector<FactorBuild> b(m);
     cudaError_t e = cudaSuccess;
@@ -812,14 +1022,36 @@ cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const st
         b[i].F = F[i];
         e = fb_sort(c, b[i]);
     }
-    // group counts, one readback
+    // group counts (and whether a run of a wide key was too long for the
+    // run sort), one readback
     uint32_t *hg = (uint32_t *)c.pinned;
-    for (size_t i = 0; i < m && e == cudaSuccess; i++)
-        if (b[i].gcount) e = cudaMemcpyAsync(hg + i, b[i].gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     std::vector<int64_t> G(m, 0);
-    if (e == cudaSuccess)
-        for (size_t i = 0; i < m; i++) G[i] = b[i].gcount ? (int64_t)hg[i] : 0;
+    for (int round = 0; round < 2 && e == cudaSuccess; round++) {
+        for (size_t i = 0; i < m; i++) hg[m + i] = 0;
+        for (size_t i = 0; i < m && e == cudaSuccess; i++) {
+            if (b[i].gcount) e = cudaMemcpyAsync(hg + i, b[i].gcount, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream);
+            if (e == cudaSuccess && b[i].too_long)
+                e = cudaMemcpyAsync(hg + m + i, b[i].too_long, sizeof(uint32_t), cudaMemcpyDeviceToHost, c.stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) break;
+        bool redo = false;
+        for (size_t i = 0; i < m; i++) {
+            G[i] = b[i].gcount ? (int64_t)hg[i] : 0;
+            if (hg[m + i]) {
+                // a run longer than the run sort takes: build it the two-word way
+                fb_free(c, b[i]);
+                factor_free(c, *b[i].F);
+                b[i] = FactorBuild{};
+                b[i].R = R[i];
+                b[i].F = F[i];
+                b[i].force_two = true;
+                if (e == cudaSuccess) e = fb_sort(c, b[i]);
+                redo = true;
+            }
+        }
+        if (!redo) break;
+    }
     for (size_t i = 0; i < m && e == cudaSuccess; i++) e = fb_groups(c, b[i], G[i]);
     if (e != cudaSuccess) {
         note_cuda_error(e, __FILE__, __LINE__);

@@ -58,6 +58,14 @@ struct Ctx {
     uint64_t launches = 0;            // kernels launched (profiling)
     int emit_rpt = 4;                 // result rows per thread of the emit kernel (2, 4 or 8)
     int tri_mode = 0;                 // triangle intersection: 0 chooses, 1 sorted lists, 2 bitmaps
+    // failure injection (tests): polls before the group scan's bounded wait
+    // gives up, whether tile 0 of that scan withholds its status (so the
+    // wait runs out), and the stream-ordered allocation to fail (counted
+    // from when the option was set; 0 = none)
+    uint32_t spin_limit = SPIN_LIMIT;
+    bool test_stall = false;
+    int64_t fail_alloc_at = 0;
+    int64_t allocs = 0;
     // device-time profile of the emit kernel (CUDA events on the stream)
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_used;     // emit kernel: start/stop pairs
@@ -73,15 +81,23 @@ struct Ctx {
 };
 
 // Stream-ordered device allocation on the context's stream.
+// An allocation the failure-injection option makes fail.
+inline bool fail_this_alloc(Ctx &c) {
+    c.allocs++;
+    return c.fail_alloc_at > 0 && c.allocs == c.fail_alloc_at;
+}
+
 template <class T>
 inline cudaError_t dalloc(Ctx &c, T **p, size_t count) {
     *p = nullptr;
+    if (fail_this_alloc(c)) return cudaErrorMemoryAllocation;
     if (count == 0) count = 1;
     if (c.pool) return cudaMallocFromPoolAsync((void **)p, count * sizeof(T), c.pool, c.stream);
     return cudaMallocAsync((void **)p, count * sizeof(T), c.stream);
 }
 inline cudaError_t dalloc_bytes(Ctx &c, void **p, size_t bytes) {
     *p = nullptr;
+    if (fail_this_alloc(c)) return cudaErrorMemoryAllocation;
     if (bytes == 0) bytes = 1;
     if (c.pool) return cudaMallocFromPoolAsync(p, bytes, c.pool, c.stream);
     return cudaMallocAsync(p, bytes, c.stream);
@@ -91,6 +107,44 @@ inline void dfree(Ctx &c, T *&p) {
     if (p) cudaFreeAsync((void *)p, c.stream);
     p = nullptr;
 }
+
+// Stream-ordered temporaries of one scope: freed when the scope ends, on
+// every path out of it (an error return included).  keep() hands one over
+// to a longer-lived owner.
+class Temps {
+  public:
+    explicit Temps(Ctx &c) : c_(c) {}
+    Temps(const Temps &) = delete;
+    Temps &operator=(const Temps &) = delete;
+    ~Temps() {
+        for (void *p : p_) cudaFreeAsync(p, c_.stream);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        cudaError_t e = dalloc(c_, p, count);
+        if (e == cudaSuccess) p_.push_back((void *)*p);
+        return e;
+    }
+    cudaError_t alloc_bytes(void **p, size_t bytes) {
+        cudaError_t e = dalloc_bytes(c_, p, bytes);
+        if (e == cudaSuccess) p_.push_back(*p);
+        return e;
+    }
+    void keep(const void *p) {
+        for (size_t i = 0; i < p_.size(); i++)
+            if (p_[i] == p) { p_.erase(p_.begin() + i); return; }
+    }
+    // frees p now (it must be one of these temporaries)
+    template <class T>
+    void free(T *&p) {
+        keep((const void *)p);
+        dfree(c_, p);
+    }
+
+  private:
+    Ctx &c_;
+    std::vector<void *> p_;
+};
 
 // ------------------------------------------------------------------ primitives
 // Exclusive prefix sums, single pass with decoupled lookback.  All of them

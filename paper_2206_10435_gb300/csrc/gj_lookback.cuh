@@ -62,15 +62,19 @@ struct SatAddU64 {
 // an aggregate.  Returns the tile's carry-in (the same in every lane) after
 // publishing its inclusive prefix.  Op must be associative and commutative
 // (the window is folded by a butterfly).
+template <class T>
+__device__ __forceinline__ void publish_aggregate(typename TileStatus<T>::W *st, uint32_t tile, T agg) {
+    TileStatus<T>::put(&st[tile], tile == 0 ? ST_P : ST_A, agg);
+}
+
+// The lookback proper, after the tile's aggregate has been published
+// (publish_aggregate by one thread, visible before any lane calls this).
 template <class T, class Op>
-__device__ __forceinline__ T warp_lookback(typename TileStatus<T>::W *st, uint32_t tile, T agg,
-                                           int lane, uint32_t *err) {
+__device__ __forceinline__ T warp_lookback_published(typename TileStatus<T>::W *st, uint32_t tile,
+                                                     T agg, int lane, uint32_t *err,
+                                                     uint32_t limit = SPIN_LIMIT) {
     Op op;
-    if (tile == 0) {
-        if (lane == 0) TileStatus<T>::put(&st[0], ST_P, agg);
-        return T(0);
-    }
-    if (lane == 0) TileStatus<T>::put(&st[tile], ST_A, agg);
+    if (tile == 0) return T(0);
     T carry = T(0);
     int64_t p = (int64_t)tile - 1;
     for (;;) {
@@ -82,7 +86,7 @@ __device__ __forceinline__ T warp_lookback(typename TileStatus<T>::W *st, uint32
             for (;;) {
                 TileStatus<T>::get(&st[q], f, v);
                 if (f) break;
-                if (++spins > SPIN_LIMIT) {
+                if (++spins > limit) {
                     raise_err(err, ERRF_TIMEOUT);
                     f = ST_P;
                     v = T(0);
@@ -101,6 +105,13 @@ __device__ __forceinline__ T warp_lookback(typename TileStatus<T>::W *st, uint32
     }
     if (lane == 0) TileStatus<T>::put(&st[tile], ST_P, op(carry, agg));
     return carry;
+}
+
+template <class T, class Op>
+__device__ __forceinline__ T warp_lookback(typename TileStatus<T>::W *st, uint32_t tile, T agg,
+                                           int lane, uint32_t *err) {
+    if (lane == 0) publish_aggregate<T>(st, tile, agg);
+    return warp_lookback_published<T, Op>(st, tile, agg, lane, err);
 }
 
 }  // namespace gj

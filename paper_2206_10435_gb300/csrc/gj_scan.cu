@@ -215,7 +215,8 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
     // layout: [counter][pad][flags (tiles)][values (tiles, 8-aligned)]
     size_t flag_bytes = ((size_t)tiles * 4 + 15) & ~(size_t)15;
     size_t bytes = 16 + flag_bytes + 2 * (size_t)tiles * sizeof(T);
-    GJ_CUDA_TRY(dalloc_bytes(c, (void **)&state, bytes));
+    Temps tmp(c);
+    GJ_CUDA_TRY(tmp.alloc_bytes((void **)&state, bytes));
     // unsegmented scans keep their status words in the value area: clear it too
     GJ_CUDA_TRY(cudaMemsetAsync(state, 0, !SEG ? bytes : 16 + flag_bytes, c.stream));
     uint32_t *counter = state;
@@ -229,9 +230,7 @@ cudaError_t launch_scan(Ctx &c, const T *in, const uint8_t *fv, const uint8_t *h
         k_scan<T, Op, ITEMS, SEG, false><<<(unsigned)tiles, SCAN_THREADS, 0, c.stream>>>(
             in, fv, heads, out, n, counter, flags, agg, inc, total, seg_total, seg_id, c.err, n_dev);
     c.launches++;
-    cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(state, c.stream);
-    return e;
+    return cudaGetLastError();
 }
 
 }  // namespace

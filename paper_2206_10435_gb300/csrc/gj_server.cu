@@ -7,11 +7,13 @@
 // the estimated device memory of all admitted requests stays under the HBM
 // budget.  Each slot is a host thread with its own CUDA stream: it gives
 // the query that stream (gj_query_set_stream), summarises it (one
-// synchronisation), desummarises the first chunk of result rows into the
-// slot's buffers and hashes the chunk on the device (one synchronisation),
-// so requests that arrive while others are on the GPU overlap with them as
-// soon as a slot and memory are free.  Times are taken on the host's steady
-// clock from the request's arrival.
+// synchronisation), then streams its result rows chunk by chunk (up to the
+// server's row limit) through the slot's buffers, hashing every chunk on the
+// device, so requests that arrive while others are on the GPU overlap with
+// them as soon as a slot and memory are free.  Admission counts the bytes the
+// context's memory pool has actually handed out plus the new request's
+// estimate.  Times are taken on the host's steady clock from the request's
+// arrival.
 #include <math.h>
 #include <string.h>
 
@@ -41,13 +43,13 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     return x;
 }
 
-__global__ void k_chunk_hash(const void *col, int width, int col_idx, int64_t n,
+__global__ void k_chunk_hash(const void *col, int width, int col_idx, uint64_t row0, int64_t n,
                              unsigned long long *h) {
     uint64_t acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t v = width == 8 ? ((const uint64_t *)col)[i] : (uint64_t)((const uint32_t *)col)[i];
-        acc ^= mix64(v ^ mix64(((uint64_t)col_idx << 40) ^ (uint64_t)i));
+        acc ^= mix64(v ^ mix64(((uint64_t)col_idx << 40) ^ (row0 + (uint64_t)i)));
     }
     for (int d = 16; d; d >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, d);
     if ((threadIdx.x & 31) == 0 && acc) atomicXor(h, (unsigned long long)acc);
@@ -70,6 +72,7 @@ struct ServerState {
     gj_ctx *ctx = nullptr;
     int n_slots = 0;
     uint64_t budget = 0, chunk = 0;
+    uint64_t max_rows = 0;                       // rows streamed per request (0: all)
     // per slot: an execution context (stream, readback buffer, error word)
     // lent to the queries the slot runs, so a request allocates nothing
     std::vector<std::unique_ptr<Ctx>> exec;
@@ -90,6 +93,18 @@ struct ServerState {
 };
 
 namespace {
+
+// bytes the context's memory pool has handed out and not taken back
+uint64_t pool_bytes(ServerState &S) {
+    cudaMemPool_t pool = S.ctx->s.c.pool;
+    if (!pool) return S.used;
+    size_t v = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) {
+        cudaGetLastError();
+        return S.used;
+    }
+    return (uint64_t)v;
+}
 
 void run_one(ServerState &S, int slot, Pending &p) {
     gj_request_result &r = S.results[p.idx];
@@ -118,24 +133,34 @@ void run_one(ServerState &S, int slot, Pending &p) {
                 bw[i] = 8;
             }
         }
-        uint64_t n = 0;
-        if (st == GJ_OK) st = desummarize(qs, 0, std::min<uint64_t>(S.chunk, total), bufs.data(),
-                                          nullptr, &n);
-        r.chunk_rows = n;
-        if (st == GJ_OK) {
-            cudaMemsetAsync(S.hash[slot], 0, 8, c.stream);
+        // stream the result (up to the row limit) chunk by chunk; the hash
+        // of every chunk accumulates on the device, and each chunk's
+        // desummarisation waits for the previous one to be hashed
+        const uint64_t want = S.max_rows ? std::min<uint64_t>(S.max_rows, total) : total;
+        if (st == GJ_OK) cudaMemsetAsync(S.hash[slot], 0, 8, c.stream);
+        uint64_t done = 0;
+        while (st == GJ_OK && done < want) {
+            uint64_t n = 0;
+            st = desummarize(qs, done, std::min<uint64_t>(S.chunk, want - done), bufs.data(), nullptr, &n);
+            if (st != GJ_OK || n == 0) break;
             for (size_t i = 0; i < widths.size(); i++) {
                 int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n, 256), c.num_sms * 4));
-                k_chunk_hash<<<grid, 256, 0, c.stream>>>(bufs[i], widths[i], (int)i, (int64_t)n,
+                k_chunk_hash<<<grid, 256, 0, c.stream>>>(bufs[i], widths[i], (int)i, done, (int64_t)n,
                                                           S.hash[slot]);
             }
+            if (done == 0) r.t_chunk = now_s();   // the first chunk is out (desummarise waited for it)
+            done += n;
+        }
+        r.rows = done;
+        if (st == GJ_OK) {
             cudaMemcpyAsync(S.hash_host[slot], S.hash[slot], 8, cudaMemcpyDeviceToHost, c.stream);
             if (cudaStreamSynchronize(c.stream) != cudaSuccess) { cudaGetLastError(); st = GJ_ERR_CUDA; }
-            r.chunk_hash = S.hash_host[slot][0];
+            r.hash = S.hash_host[slot][0];
         }
     }
     r.status = st;
-    r.t_chunk = now_s();
+    r.t_last = now_s();
+    if (r.t_chunk == 0) r.t_chunk = r.t_last;
 }
 
 void worker(ServerState *S, int slot) {
@@ -148,7 +173,23 @@ void worker(ServerState *S, int slot) {
             for (;;) {
                 if (!S->pending.empty()) {
                     Pending &h = S->pending.front();
-                    if (S->used + h.est <= S->budget || S->in_flight == 0) break;
+                    // bytes the pool has handed out (resident factors, the
+                    // summaries and buffers of the requests in flight) plus
+                    // the new request's estimate
+                    const uint64_t in_use = pool_bytes(*S) ;
+                    if (in_use + h.est <= S->budget) break;
+                    if (S->in_flight == 0) {
+                        // nothing will free memory: it can never be admitted
+                        Pending p = h;
+                        S->pending.pop_front();
+                        gj_request_result &r = S->results[p.idx];
+                        r.status = GJ_ERR_OOM;
+                        r.t_admit = r.t_summary = r.t_chunk = r.t_last = now_s();
+                        gj_query_destroy(p.q);
+                        S->remaining--;
+                        S->cv.notify_all();
+                        continue;
+                    }
                 }
                 if (S->stop && S->pending.empty()) return;
                 S->cv.wait(lk);
@@ -156,7 +197,7 @@ void worker(ServerState *S, int slot) {
             p = S->pending.front();
             S->pending.pop_front();
             S->used += p.est;
-            S->peak_used = std::max(S->peak_used, S->used);
+            S->peak_used = std::max(S->peak_used, pool_bytes(*S) + p.est);
             S->in_flight++;
             S->peak_in_flight = std::max(S->peak_in_flight, S->in_flight);
             S->results[p.idx].t_admit = now_s();
@@ -185,7 +226,7 @@ using namespace gj;
 extern "C" {
 
 gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, uint64_t chunk_rows,
-                           gj_server **out) {
+                           uint64_t max_rows, gj_server **out) {
     if (!ctx || !out || n_slots < 1 || n_slots > 256 || chunk_rows < 1 || chunk_rows > (1ull << 31))
         return GJ_ERR_INVALID;
     *out = nullptr;
@@ -195,6 +236,7 @@ gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, ui
     S.n_slots = n_slots;
     S.budget = hbm_budget;
     S.chunk = chunk_rows;
+    S.max_rows = max_rows;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->s.c.device);
@@ -263,7 +305,7 @@ gj_status gj_server_run(gj_server *sv, int32_t n_requests, const int32_t *rel_id
         gj_status st = gj_query_create(S.ctx, rel_ids + query_off[i], query_off[i + 1] - query_off[i], &q);
         if (st != GJ_OK) {
             r.status = st;
-            r.t_summary = r.t_chunk = now_s();
+            r.t_summary = r.t_chunk = r.t_last = now_s();
             std::lock_guard<std::mutex> lk(S.mu);
             S.remaining--;
             continue;
@@ -276,7 +318,7 @@ gj_status gj_server_run(gj_server *sv, int32_t n_requests, const int32_t *rel_id
         r.est_bytes = est;
         if (est > S.budget) {
             r.status = GJ_ERR_OOM;   // can never be admitted
-            r.t_summary = r.t_chunk = now_s();
+            r.t_summary = r.t_chunk = r.t_last = now_s();
             gj_query_destroy(q);
             std::lock_guard<std::mutex> lk(S.mu);
             S.remaining--;

@@ -49,10 +49,19 @@ k_digit_hist(const uint64_t *__restrict__ keys, PackSrc ps, int64_t n, int lo_bi
     __shared__ uint32_t sh[RS_MAX_PASSES][RS_RADIX];
     for (int i = threadIdx.x; i < RS_MAX_PASSES * RS_RADIX; i += RS_THREADS) (&sh[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * RS_THREADS) {
-        const uint64_t k = PACK ? pack_word(ps, i) : keys[i];
-        for (int p = 0; p < passes; p++) atomicAdd(&sh[p][(k >> (lo_bit + 8 * p)) & 0xff], 1u);
+    // four words per thread and round, their loads issued together
+    const int64_t stride = (int64_t)gridDim.x * RS_THREADS;
+    for (int64_t i0 = (int64_t)blockIdx.x * RS_THREADS + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        uint64_t k[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t i = i0 + u * stride;
+            k[u] = i < n ? (PACK ? pack_word(ps, i) : __ldg((const unsigned long long *)keys + i)) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u * stride < n)
+                for (int p = 0; p < passes; p++) atomicAdd(&sh[p][(k[u] >> (lo_bit + 8 * p)) & 0xff], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * RS_RADIX; i += RS_THREADS) {
@@ -281,10 +290,11 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
     uint64_t *k2 = nullptr;
     uint32_t *v2 = nullptr, *hist = nullptr, *counters = nullptr;
     unsigned long long *status = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &k2, n));
-    GJ_CUDA_TRY(dalloc(c, &v2, n));
-    GJ_CUDA_TRY(dalloc(c, &hist, RS_MAX_PASSES * RS_RADIX + passes));
-    GJ_CUDA_TRY(dalloc(c, &status, (size_t)tiles * RS_RADIX));
+    Temps tmp(c);
+    GJ_CUDA_TRY(tmp.alloc(&k2, n));
+    GJ_CUDA_TRY(tmp.alloc(&v2, n));
+    GJ_CUDA_TRY(tmp.alloc(&hist, RS_MAX_PASSES * RS_RADIX + passes));
+    GJ_CUDA_TRY(tmp.alloc(&status, (size_t)tiles * RS_RADIX));
     counters = hist + RS_MAX_PASSES * RS_RADIX;
     GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + passes),
                                 c.stream));
@@ -307,10 +317,6 @@ cudaError_t radix_sort_u64_u32(Ctx &c, uint64_t *keys, uint32_t *vals, int64_t n
         GJ_CUDA_TRY(cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, c.stream));
         GJ_CUDA_TRY(cudaMemcpyAsync(vals, va, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, c.stream));
     }
-    dfree(c, k2);
-    dfree(c, v2);
-    dfree(c, hist);
-    dfree(c, status);
     return cudaSuccess;
 }
 
@@ -432,12 +438,13 @@ cudaError_t radix_sort_words(Ctx &c, const PackSrc *pack, uint64_t *keys, uint64
     const int64_t tiles = ceil_div(n, RS_TILE);
     uint32_t *hist = nullptr;
     unsigned long long *status = nullptr;
-    GJ_CUDA_TRY(dalloc(c, &hist, RS_MAX_PASSES * RS_RADIX + RS_MAX_PASSES));
-    GJ_CUDA_TRY(dalloc(c, &status, (size_t)tiles * RS_RADIX));
+    Temps tmp(c);
+    GJ_CUDA_TRY(tmp.alloc(&hist, RS_MAX_PASSES * RS_RADIX + RS_MAX_PASSES));
+    GJ_CUDA_TRY(tmp.alloc(&status, (size_t)tiles * RS_RADIX));
     uint32_t *counters = hist + RS_MAX_PASSES * RS_RADIX;
     GJ_CUDA_TRY(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * (RS_MAX_PASSES * RS_RADIX + RS_MAX_PASSES), c.stream));
     const PackSrc ps = pack ? *pack : PackSrc{};
-    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 4);
+    int hist_blocks = (int)std::min<int64_t>(ceil_div(n, RS_THREADS * 16), (int64_t)c.num_sms * 8);
     if (hist_blocks < 1) hist_blocks = 1;
     if (pack)
         k_digit_hist<true><<<hist_blocks, RS_THREADS, 0, c.stream>>>(nullptr, ps, n, lo_bit, passes, hist);
@@ -475,8 +482,6 @@ cudaError_t radix_sort_words(Ctx &c, const PackSrc *pack, uint64_t *keys, uint64
     }
     *kres = ka;
     if (vres) *vres = va;
-    dfree(c, hist);
-    dfree(c, status);
     return cudaSuccess;
 }
 

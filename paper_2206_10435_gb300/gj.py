@@ -24,6 +24,9 @@ GJ_OK, GJ_ERR_INVALID, GJ_ERR_NOT_ACYCLIC, GJ_ERR_OOM, GJ_ERR_OVERFLOW, GJ_ERR_C
 GJ_REL_BORROW, GJ_REL_COPY, GJ_REL_HOST = 0, 1, 2
 GJ_OPT_EMIT_ROWS_PER_THREAD = 1
 GJ_OPT_TRIANGLE_INTERSECT = 2   # 0 chooses, 1 sorted lists, 2 bitmaps
+GJ_OPT_SPIN_LIMIT = 3           # failure injection: polls of the group scan's bounded wait
+GJ_OPT_TEST_STALL = 4           # failure injection: that wait runs out
+GJ_OPT_FAIL_ALLOC_AT = 5        # failure injection: the N-th device allocation fails
 SAT = (1 << 64) - 1
 
 
@@ -56,10 +59,10 @@ class Profile(ctypes.Structure):
 
 class RequestResult(ctypes.Structure):
     _fields_ = [("total", ctypes.c_uint64), ("status", ctypes.c_int32), ("slot", ctypes.c_int32),
-                ("chunk_rows", ctypes.c_uint64), ("chunk_hash", ctypes.c_uint64),
+                ("rows", ctypes.c_uint64), ("hash", ctypes.c_uint64),
                 ("est_bytes", ctypes.c_uint64), ("t_arrival", ctypes.c_double),
                 ("t_admit", ctypes.c_double), ("t_summary", ctypes.c_double),
-                ("t_chunk", ctypes.c_double)]
+                ("t_chunk", ctypes.c_double), ("t_last", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -97,6 +100,11 @@ def lib() -> ctypes.CDLL:
         "gj_destroy": (None, [_P]),
         "gj_set_stream": (ctypes.c_int, [_P, _P]),
         "gj_set_option": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64]),
+        "gj_pool_usage": (ctypes.c_int, [_P, _P, _P]),
+        "gj_shard_domain": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+        "gj_shard_up": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int64]),
+        "gj_shard_down": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
+                                         _P, _P]),
         "gj_profile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Profile)]),
         "gj_load_relation": (ctypes.c_int, [_P, ctypes.POINTER(RelationDesc),
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -131,7 +139,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_int32)]),
         "gj_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
         "gj_batch_destroy": (None, [_P]),
-        "gj_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64,
+        "gj_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                             ctypes.POINTER(_P)]),
         "gj_server_run": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32),
@@ -203,6 +211,14 @@ class Context:
 
     def set_option(self, option: int, value: int):
         _check(lib().gj_set_option(self.h, option, value), "gj_set_option")
+
+    def pool_usage(self):
+        """(bytes the context's pool has handed out, device allocations made
+        since GJ_OPT_FAIL_ALLOC_AT was last set)."""
+        used = ctypes.c_uint64()
+        n = ctypes.c_int64()
+        _check(lib().gj_pool_usage(self.h, ctypes.byref(used), ctypes.byref(n)), "gj_pool_usage")
+        return int(used.value), int(n.value)
 
     def profile(self, enable: bool = True) -> dict:
         """Counters since the last call (synchronises), then profiling on/off."""
@@ -333,6 +349,51 @@ class Query:
         _check(st, "gj_summarize")
         return self.total
 
+    # ---- one rank's part of a row-sharded counting pass (gj_shard_*)
+    def children(self, rel: int):
+        """rel's children in the join tree, in position order."""
+        return [j for j, p in enumerate(self.parent) if p == rel]
+
+    def shard_domain(self, rel: int):
+        """(lo, hi) of rel's separator attribute over this rank's rows."""
+        lo, hi = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().gj_shard_domain(self.h, rel, ctypes.byref(lo), ctypes.byref(hi)), "gj_shard_domain")
+        return int(lo.value), int(hi.value)
+
+    def _children_args(self, rel, msgs):
+        ch = self.children(rel)
+        ptrs = (_P * max(len(ch), 1))(*[_ptr(msgs[c][0]) for c in ch])
+        los = _i32([msgs[c][1] for c in ch] or [0])
+        lens = (ctypes.c_int64 * max(len(ch), 1))(*[int(msgs[c][0].numel()) for c in ch])
+        return ch, ptrs, los, lens
+
+    def shard_up(self, rel: int, msgs, lo: int = 0, length: int = 1):
+        """rel's partial message on this rank (int64 tensor holding uint64
+        bits; one entry, the partial join size, for the root).  msgs[c] =
+        (global message tensor, lo) of each child c."""
+        torch = self.ctx.torch
+        dev = torch.device("cuda", self.ctx.device)
+        n = 1 if self.parent[rel] < 0 else length
+        out = torch.empty(n, dtype=torch.int64, device=dev)
+        _, ptrs, los, lens = self._children_args(rel, msgs)
+        _check(lib().gj_shard_up(self.h, rel, ptrs, los, lens, _P(_ptr(out)), lo, n), "gj_shard_up")
+        return out
+
+    def shard_down(self, rel: int, down, msgs):
+        """Partial down messages to rel's children and rel's local partial
+        multiplicities, given rel's global down message (tensor, lo) (None
+        for the root) and the children's global messages."""
+        torch = self.ctx.torch
+        dev = torch.device("cuda", self.ctx.device)
+        ch, ptrs, los, lens = self._children_args(rel, msgs)
+        outs = [torch.empty(int(msgs[c][0].numel()), dtype=torch.int64, device=dev) for c in ch]
+        optrs = (_P * max(len(ch), 1))(*[_ptr(o) for o in outs])
+        mult = torch.empty(max(self.n_groups[rel], 1), dtype=torch.int64, device=dev)
+        dptr, dlo, dlen = (_P(_ptr(down[0])), down[1], int(down[0].numel())) if down is not None else (None, 0, 0)
+        _check(lib().gj_shard_down(self.h, rel, dptr, dlo, dlen, ptrs, los, lens, optrs, _P(_ptr(mult))),
+               "gj_shard_down")
+        return dict(zip(ch, outs)), mult[:self.n_groups[rel]]
+
     def summary_groups(self, rel: int):
         torch = self.ctx.torch
         G = self.n_groups[rel]
@@ -440,10 +501,12 @@ class NativeServer:
     """The native serving runtime (gj_server_*): replays arrival traces."""
 
     def __init__(self, ctx: Context, n_slots: int = 16, hbm_budget: int = 150 * 10**9,
-                 chunk_rows: int = 1 << 20):
+                 chunk_rows: int = 1 << 20, max_rows: int = 0):
+        """max_rows: result rows streamed per request (0: the whole result),
+        in chunks of chunk_rows."""
         self.ctx = ctx
         h = _P()
-        _check(lib().gj_server_create(ctx.h, n_slots, hbm_budget, chunk_rows, ctypes.byref(h)),
+        _check(lib().gj_server_create(ctx.h, n_slots, hbm_budget, chunk_rows, max_rows, ctypes.byref(h)),
                "gj_server_create")
         self.h = h
 

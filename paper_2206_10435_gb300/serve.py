@@ -39,7 +39,9 @@ class Request:
     status: str = "pending"
     t_admit: float = 0.0
     t_summary: float = 0.0
-    t_chunk: float = 0.0
+    t_chunk: float = 0.0           # first result chunk out
+    t_last: float = 0.0            # last result chunk out
+    rows: int = 0                  # result rows streamed
     slot: int = -1
     result: object = None          # engine-specific (checksum or host copy)
 
@@ -175,11 +177,15 @@ def native_latency_stats(results):
         return {"completed": 0}
     s = np.array([r["t_summary"] - r["t_arrival"] for r in ok]) * 1000
     c = np.array([r["t_chunk"] - r["t_arrival"] for r in ok]) * 1000
-    span = max(r["t_chunk"] for r in ok) - min(r["t_arrival"] for r in ok)
+    last = np.array([r["t_last"] - r["t_arrival"] for r in ok]) * 1000
+    span = max(r["t_last"] for r in ok) - min(r["t_arrival"] for r in ok)
+    rows = sum(int(r["rows"]) for r in ok)
     return {"completed": len(ok), "failed": len(results) - len(ok),
             "qps": len(ok) / span if span > 0 else None,
+            "rows_streamed": rows, "rows_per_s": rows / span if span > 0 else None,
             "p50_summary_ms": float(np.percentile(s, 50)), "p99_summary_ms": float(np.percentile(s, 99)),
-            "p50_first_chunk_ms": float(np.percentile(c, 50)), "p99_first_chunk_ms": float(np.percentile(c, 99))}
+            "p50_first_chunk_ms": float(np.percentile(c, 50)), "p99_first_chunk_ms": float(np.percentile(c, 99)),
+            "p50_last_chunk_ms": float(np.percentile(last, 50)), "p99_last_chunk_ms": float(np.percentile(last, 99))}
 
 
 def latency_stats(reqs):
@@ -189,27 +195,32 @@ def latency_stats(reqs):
         return {"completed": 0}
     s = np.array([r.t_summary - r.arrival for r in ok]) * 1000
     c = np.array([r.t_chunk - r.arrival for r in ok]) * 1000
-    span = max(r.t_chunk for r in ok) - min(r.arrival for r in ok)
+    last = np.array([max(r.t_last, r.t_chunk) - r.arrival for r in ok]) * 1000
+    span = max(max(r.t_last, r.t_chunk) for r in ok) - min(r.arrival for r in ok)
+    rows = sum(r.rows for r in ok)
     return {"completed": len(ok), "rejected": sum(r.status == "rejected" for r in reqs),
             "errors": sum(r.status.startswith("error") for r in reqs),
             "qps": len(ok) / span if span > 0 else None,
+            "rows_streamed": rows, "rows_per_s": rows / span if span > 0 else None,
             "p50_summary_ms": float(np.percentile(s, 50)), "p99_summary_ms": float(np.percentile(s, 99)),
-            "p50_first_chunk_ms": float(np.percentile(c, 50)), "p99_first_chunk_ms": float(np.percentile(c, 99))}
+            "p50_first_chunk_ms": float(np.percentile(c, 50)), "p99_first_chunk_ms": float(np.percentile(c, 99)),
+            "p50_last_chunk_ms": float(np.percentile(last, 50)), "p99_last_chunk_ms": float(np.percentile(last, 99))}
 
 
 class GJEngine(Engine):
     """Runs a request through the C ABI: plan (gj_query_create with resident
-    factors), then on the slot's stream summarise and desummarise the first
-    chunk into the slot's buffers."""
+    factors), then on the slot's stream summarise and stream the result rows
+    (up to max_rows, 0 = all) chunk by chunk through the slot's buffers."""
 
     def __init__(self, ctx, n_slots: int, chunk_rows: int = 1 << 20, keep_results: bool = False,
-                 max_cols: int = 16):
+                 max_cols: int = 16, max_rows: int = 0):
         import torch
         from . import gj
         self.torch = torch
         self.gj = gj
         self.ctx = ctx
         self.chunk = chunk_rows
+        self.max_rows = max_rows
         self.keep = keep_results
         dev = torch.device("cuda", ctx.device)
         self.streams = [torch.cuda.Stream(dev) for _ in range(n_slots)]
@@ -238,7 +249,7 @@ class GJEngine(Engine):
                 req.status = "overflow"
             req.t_summary = time.perf_counter()
             if req.status == "pending" and req.total > 0:
-                n = min(self.chunk, req.total)
+                want = min(self.max_rows, req.total) if self.max_rows else req.total
                 widths = q.col_width
                 buf = self.bufs[slot]
                 if buf is None or len(buf) != len(widths) or any(
@@ -246,11 +257,21 @@ class GJEngine(Engine):
                     buf = [torch.empty(self.chunk, dtype=torch.int32 if w == 4 else torch.int64,
                                        device=self.dev) for w in widths]
                     self.bufs[slot] = buf
-                cols = q.desummarize(0, n, out=buf)
+                kept = []
+                for r0 in range(0, want, self.chunk):
+                    cols = q.desummarize(r0, min(self.chunk, want - r0), out=buf)
+                    if self.keep:
+                        kept.append([c.cpu() for c in cols])
+                    if r0 == 0:
+                        st.synchronize()
+                        req.t_chunk = time.perf_counter()
+                req.rows = want
                 if self.keep:
-                    req.result = [c.cpu() for c in cols]
+                    req.result = [torch.cat([k[i] for k in kept]) for i in range(len(widths))]
             st.synchronize()
-            req.t_chunk = time.perf_counter()
+            req.t_last = time.perf_counter()
+            if not req.t_chunk:
+                req.t_chunk = req.t_last
 
     def release(self, req: Request):
         if req.plan is not None:

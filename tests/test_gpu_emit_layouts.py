@@ -192,3 +192,26 @@ def test_pinned_host_columns_from_fresh_threads(kctx):
     for qq in qs:
         qq.close()
     run.close()
+
+
+def test_emit_autotuner_picks_a_choice_and_results_stay_exact(kctx, tmp_path):
+    """tune_emit times the emit's rows per thread on a real window, caches
+    the choice per GPU and result shape, and leaves it set; the rows are the
+    oracle's whichever it picks."""
+    from paper_2206_10435_gb300 import autotune, gj
+    q = G.chain3_uniform(seed=31, rows=3000, end_domain=600, mid_domain=50)
+    run = Run(kctx, q)
+    run.summarize()
+    cache = str(tmp_path / "tune.json")
+    first = autotune.tune_emit(kctx, run.q, window=1 << 16, reps=1, cache_path=cache)
+    assert first["rpt"] in (2, 4, 8) and not first["cached"]
+    assert set(first["candidates_ms"]) == {"2", "4", "8"}
+    again = autotune.tune_emit(kctx, run.q, window=1 << 16, reps=1, cache_path=cache)
+    assert again["cached"] and again["rpt"] == first["rpt"]
+    ref = O.join(q)
+    cols, rids = run.rows()
+    assert np.array_equal(rids, ref.rowids)
+    for a, b in zip(cols, O.columns(q, ref.rowids)):
+        assert np.array_equal(a, b)
+    kctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, 4)
+    run.close()

@@ -212,63 +212,131 @@ def test_factor_matches_stable_sort(ctx):
     ctx.release_relation(rid)
 
 
-def _sampled_group_mult(q, c, run, rel, n_sample=2000, seed=0):
-    """Oracle multiplicities of a sample of the GPU's groups."""
+def _check_factor(ctx, rid, cols, order, n):
+    perm, gstart, gkey = ctx.factor_export(rid, n, len(cols), order)
+    ref = np.lexsort([cols[c] for c in reversed(order)])   # stable: row id breaks ties
+    assert np.array_equal(perm.cpu().numpy(), ref)
+    srt = np.stack([cols[c][ref] for c in range(len(cols))], axis=1)
+    head = np.ones(n, bool)
+    head[1:] = (srt[1:] != srt[:-1]).any(axis=1)
+    starts = np.flatnonzero(head)
+    assert np.array_equal(gstart.cpu().numpy()[:-1], starts)
+    assert int(gstart[-1]) == n
+    assert np.array_equal(gkey.cpu().numpy().T, srt[starts])
+
+
+@pytest.mark.parametrize("long_run", [False, True])
+def test_factor_wide_keys_match_stable_sort(ctx, long_run):
+    """Keys of three 22-bit columns (66 bits: with the row id they need two
+    words).  The rows are sorted by the leading columns, then run by run by
+    the rest; runs of up to 256 rows are sorted by one warp.  A run longer
+    than that (long_run) sends the factor down the two-word path instead;
+    both give the stable sort."""
+    rng = np.random.default_rng(11)
+    n = 100_000
+    spread = lambda k: rng.choice(np.linspace(-(1 << 21), (1 << 21) - 1, k).astype(np.int32), n)
+    c0, c1 = spread(40), spread(40)
+    c2 = rng.integers(-(1 << 21), 1 << 21, n, dtype=np.int32)
+    c2[::7] = 5                       # repeated full keys: rows tie on the key
+    if long_run:
+        c0[:1000] = c0[0]
+        c1[:1000] = c1[0]
+    cols = [c0, c1, c2]
+    rid = ctx.load_relation([torch.from_numpy(c).cuda() for c in cols], [0, 1, 2])
+    for order in ([0, 1, 2], [2, 0, 1], [1, 0, 2]):
+        _check_factor(ctx, rid, cols, order, n)
+    ctx.release_relation(rid)
+
+
+def _all_group_mult(q, c, run, rel):
+    """Every group of relation rel against the oracle's counting pass, in
+    O(rows): every row of a group holds the group's key tuple, groups are
+    strictly increasing in the factor's column order (so they are the
+    distinct key tuples), and a group's multiplicity is the sum of the
+    oracle's per-row multiplicities over its rows.  Returns (keys in
+    declared column order, multiplicities) in group order."""
     R = q.relations[rel]
-    perm, gstart, gkey = run.ctx.factor_export(run.ids[rel], R.n_rows, len(R.keys),
-                                               run.factor_order(rel))
+    order = run.factor_order(rel)
+    perm, gstart, gkey = run.ctx.factor_export(run.ids[rel], R.n_rows, len(R.keys), order)
     _, m, _ = run.q.summary_groups(rel)
-    keys = gkey.cpu().numpy().T
-    mult = to_u64(m)
-    rng = np.random.default_rng(seed)
-    pick = rng.choice(keys.shape[0], size=min(n_sample, keys.shape[0]), replace=False)
-    packed = np.zeros(R.n_rows, dtype=np.int64)
-    for col in R.keys:
-        packed = packed * (1 << 32) + (col.astype(np.int64) & 0xFFFFFFFF) if len(R.keys) <= 2 else None
-    want = {}
-    for g in pick.tolist():
-        pk = 0
-        for v in keys[g].tolist():
-            pk = pk * (1 << 32) + (v & 0xFFFFFFFF)
-        want[pk] = g
-    sel = np.isin(packed, np.array(list(want.keys()), dtype=np.int64))
-    rows = np.flatnonzero(sel)
-    acc = {}
-    for r, v in zip(rows.tolist(), c.mult[rel][rows].tolist()):
-        acc[int(packed[r])] = acc.get(int(packed[r]), 0) + int(v)
-    for pk, g in want.items():
-        assert acc.get(pk, 0) == int(mult[g])
+    perm = perm.cpu().numpy().astype(np.int64)
+    gs = gstart.cpu().numpy().astype(np.int64)
+    keys = gkey.cpu().numpy()                     # [column][group]
+    G = keys.shape[1]
+    sizes = np.diff(gs)
+    assert sizes.min() >= 1 and gs[-1] == R.n_rows
+    for col in range(len(R.keys)):
+        assert np.array_equal(R.keys[col][perm], np.repeat(keys[col], sizes)), (rel, col)
+    if G > 1:   # strictly increasing, most significant column first
+        diff = np.zeros(G - 1, dtype=np.int8)
+        for col in reversed(order):
+            d = np.sign(keys[col][1:].astype(np.int64) - keys[col][:-1])
+            diff = np.where(d != 0, d, diff)
+        assert (diff > 0).all(), rel
+    row_mult = c.mult[rel].astype(np.uint64)[perm]
+    want = np.add.reduceat(row_mult, gs[:-1]) if G else np.zeros(0, np.uint64)
+    got = to_u64(m)
+    assert np.array_equal(got, want), rel
+    return keys.T, got
 
 
-@pytest.mark.parametrize("scale", ["full"])
-def test_chain5_zipf_full_size(ctx, scale):
-    """5-chain, 10^7 rows per table, Zipf(1.1) over 10^6: exact total and
-    sampled multiplicities against the oracle's counting pass; windows of
-    2^28 rows checked by properties that pin them to the sorted result."""
+def test_chain5_zipf_full_size(ctx):
+    """5-chain, 10^7 rows per table, Zipf(1.1) over 10^6: exact total, the
+    multiplicity of every group of every relation against the oracle's
+    counting pass, GFJS level 0 against the per-value marginal of K0, and
+    every 2^28-row window checked by properties that pin it to the sorted
+    result."""
     q = G.chain5_zipf()
     c = O.count(q, rows=True)
     run = Run(ctx, q)
     total = run.summarize()
     assert total == c.total
-    for rel in range(5):
-        _sampled_group_mult(q, c, run, rel)
-    dev = device_columns(torch, q)
+    got = [_all_group_mult(q, c, run, rel) for rel in range(5)]
+    # level 0 (V[0] = K0, held by R1's first column): one run per K0 value,
+    # its frequency the marginal of that value = summed multiplicities of
+    # R1's key tuples with it (Section 1.2)
+    allk, m = got[0]
     pl = O.plan(q)
+    col = q.relations[0].attrs.index(pl.V[0])
+    vals, inv = np.unique(allk[:, col], return_inverse=True)
+    marg = np.zeros(vals.shape[0], dtype=np.uint64)
+    np.add.at(marg, inv.reshape(-1), m)
+    live = marg > 0
+    # runs are returned by the window of result rows they start in; the
+    # windows partition the level
+    parts = [run.q.level(0, r0, 1 << 28, cap=int(live.sum())) for r0 in range(0, total, 1 << 28)]
+    val = np.concatenate([p[0].cpu().numpy() for p in parts])
+    freq = np.concatenate([to_u64(p[1]) for p in parts])
+    off = np.concatenate([to_u64(p[2]) for p in parts])
+    assert np.array_equal(val, vals[live].astype(np.int32))
+    assert np.array_equal(freq, marg[live])
+    want_off = np.concatenate([[0], np.cumsum(marg[live])[:-1]]).astype(np.uint64)
+    assert np.array_equal(off, want_off)
+    dev = device_columns(torch, q)
     W = 1 << 28
-    # first, a middle and the last (ragged) window
-    for r0 in (0, (total // 2 // W) * W, (total // W) * W):
+    last = None
+    done = 0
+    for r0 in range(0, total, W):
         out, rids = run.q.desummarize(r0, W, rowids=True)
-        check_canonical_window(torch, q, pl, dev, out, rids)
+        last = check_canonical_window(torch, q, pl, dev, out, rids, last)
         assert out[0].shape[0] == min(W, total - r0)
+        done += out[0].shape[0]
+        del out, rids
+    assert done == total
     run.close()
 
 
 def test_star_full_size(ctx):
+    """Star, fact table 10^8 rows: exact total, the multiplicity of every
+    group of the fact and dimension tables against the oracle's counting
+    pass, and every window checked by the canonical-order properties."""
     q = G.star_poisson()
-    c = O.count(q)
+    c = O.count(q, rows=True)
     run = Run(ctx, q)
     total = run.summarize()
     assert total == c.total
+    for rel in range(len(q.relations)):
+        _all_group_mult(q, c, run, rel)
     dev = device_columns(torch, q)
     pl = O.plan(q)
     W = 1 << 28
@@ -278,6 +346,7 @@ def test_star_full_size(ctx):
         out, rids = run.q.desummarize(r0, W, rowids=True)
         last = check_canonical_window(torch, q, pl, dev, out, rids, last)
         done += out[0].shape[0]
+        del out, rids
     assert done == total
     run.close()
 

@@ -35,7 +35,7 @@ def test_results_alone_equal_results_in_the_mix():
     chunk = 1 << 14
     # alone: one slot, one request at a time
     alone = {}
-    eng1 = GJEngine(ctx, 1, chunk_rows=chunk, keep_results=True)
+    eng1 = GJEngine(ctx, 1, chunk_rows=chunk, keep_results=True, max_rows=3 * chunk + 5)
     srv1 = Server(eng1, n_slots=1)
     for i, q in enumerate(ids):
         r = Request(i, q)
@@ -49,7 +49,7 @@ def test_results_alone_equal_results_in_the_mix():
     # mixed: 8 slots, 300 requests arriving much faster than they are served
     rng = np.random.default_rng(9)
     picks = rng.integers(0, len(ids), size=300)
-    eng8 = GJEngine(ctx, 8, chunk_rows=chunk, keep_results=True)
+    eng8 = GJEngine(ctx, 8, chunk_rows=chunk, keep_results=True, max_rows=3 * chunk + 5)
     srv8 = Server(eng8, n_slots=8)
     reqs = run_stream(srv8, [ids[p] for p in picks], poisson_arrivals(50000.0, 300, seed=3))
     assert srv8.peak_in_flight > 1

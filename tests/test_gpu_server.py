@@ -1,6 +1,8 @@
 """The native serving runtime (gj_server_*): join sizes against the oracle,
-and every request's first result chunk (by its hash) identical when the
-request runs alone and when it runs mixed with concurrent requests."""
+and every request's streamed result (all its chunks, by their hash)
+identical when the request runs alone and when it runs mixed with
+concurrent requests; the hash of a request's rows equals the hash of the
+oracle's result columns."""
 import numpy as np
 import pytest
 
@@ -24,6 +26,27 @@ def _pool(n=20, seed=8):
     return qs
 
 
+def _mix64(x):
+    M = (1 << 64) - 1
+    x ^= x >> 30
+    x = (x * 0xbf58476d1ce4e5b9) & M
+    x ^= x >> 27
+    x = (x * 0x94d049bb133111eb) & M
+    x ^= x >> 31
+    return x
+
+
+def _hash_columns(cols):
+    """The server's hash of result rows 0..n-1: xor over columns c and rows i
+    of mix(v ^ mix(c << 40 ^ i)), v the value as an unsigned 32/64-bit word."""
+    h = 0
+    for c, col in enumerate(cols):
+        bits = 32 if col.dtype.itemsize == 4 else 64
+        for i, v in enumerate(col.tolist()):
+            h ^= _mix64((int(v) & ((1 << bits) - 1)) ^ _mix64((c << 40) ^ i))
+    return h
+
+
 def test_native_server_alone_equals_mix():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -35,22 +58,29 @@ def test_native_server_alone_equals_mix():
     for q in ids:
         ctx.query(q).close()
     chunk = 1 << 13
-    one = gj.NativeServer(ctx, n_slots=1, chunk_rows=chunk)
+    limit = 5 * chunk + 17         # several chunks and a ragged last one
+    one = gj.NativeServer(ctx, n_slots=1, chunk_rows=chunk, max_rows=limit)
     alone, _ = one.run(ids, np.arange(len(ids)) * 0.002)
     one.close()
     for r, t in zip(alone, ref):
         assert r["status"] == gj.GJ_OK and r["total"] == t
-        assert r["chunk_rows"] == min(chunk, t)
+        assert r["rows"] == min(limit, t)
+        assert r["t_last"] >= r["t_chunk"] >= r["t_summary"] >= r["t_arrival"]
+    # the hash of the streamed rows is the hash of the oracle's columns
+    for q, r in list(zip(pool, alone))[:6]:
+        j = O.join(q)
+        cols = O.columns(q, j.rowids[:r["rows"]])
+        assert r["hash"] == _hash_columns(cols)
     rng = np.random.default_rng(4)
     picks = rng.integers(0, len(ids), size=400)
-    many = gj.NativeServer(ctx, n_slots=8, chunk_rows=chunk)
+    many = gj.NativeServer(ctx, n_slots=8, chunk_rows=chunk, max_rows=limit)
     mix, stats = many.run([ids[p] for p in picks], np.zeros(400))
     many.close()
     assert stats["peak_in_flight"] > 1
     for r, p in zip(mix, picks):
         a = alone[int(p)]
         assert r["status"] == gj.GJ_OK
-        assert (r["total"], r["chunk_rows"], r["chunk_hash"]) == (a["total"], a["chunk_rows"], a["chunk_hash"])
+        assert (r["total"], r["rows"], r["hash"]) == (a["total"], a["rows"], a["hash"])
     # admission never exceeds the budget; a request larger than it is refused
     tiny = gj.NativeServer(ctx, n_slots=4, hbm_budget=1, chunk_rows=chunk)
     res, st = tiny.run(ids[:3], [0.0, 0.0, 0.0])

@@ -134,3 +134,142 @@ def _rank_rows(rank, world, port, out):
 def test_two_gloo_ranks_result_ranges_concatenate_to_the_join():
     res = _spawn(_rank_rows, 2)
     assert all(ok for _, ok, n in res) and res[0][2] > 0
+
+
+# ---- the row-sharded counting pass (paper_2206_10435_gb300/shard.py) ----
+
+def _plan_parent_sep(query):
+    """Join tree by the library's rule: relation j hangs under the first
+    earlier relation holding every attribute j shares with relations
+    before it; the separator is that (single) shared attribute."""
+    parent, sep, seen = [-1], [None], set(query.relations[0].attrs)
+    for j, R in enumerate(query.relations[1:], 1):
+        shared = [a for a in R.attrs if a in seen]
+        assert len(shared) == 1
+        parent.append(next(i for i in range(j) if shared[0] in query.relations[i].attrs))
+        sep.append(shared[0])
+        seen.update(R.attrs)
+    return parent, sep
+
+
+class NumpyShard:
+    """A rank's part of the sharded pass computed on the CPU from the
+    definitions, row by row (each row is a group of count 1; sums over rows
+    equal sums over groups), with Python integers.  It stands in for the
+    GPU engine so that the coordination and the collectives run on gloo."""
+
+    def __init__(self, query, rank, world):
+        from paper_2206_10435_gb300 import shard as S
+        self.parent, self.sep = _plan_parent_sep(query)
+        self.attrs = [R.attrs for R in query.relations]
+        self.keys = []
+        for R in query.relations:
+            lo, hi = S.rows_of(R.n_rows, rank, world)
+            self.keys.append([k[lo:hi].astype(np.int64) for k in R.keys])
+        self.children = {t: [j for j, p in enumerate(self.parent) if p == t]
+                         for t in range(len(self.parent))}
+        self.local_keys = {}
+
+    def col(self, rel, attr):
+        return self.keys[rel][self.attrs[rel].index(attr)]
+
+    def shard_domain(self, rel):
+        v = np.concatenate([self.col(rel, self.sep[rel]), self.col(self.parent[rel], self.sep[rel])])
+        return (int(v.min()), int(v.max())) if v.size else (1, 0)
+
+    def _at(self, rel, c, msgs):
+        vec, lo = msgs[c]
+        idx = self.col(rel, self.sep[c]) - lo
+        ok = (idx >= 0) & (idx < vec.shape[0])
+        out = np.zeros(idx.shape[0], dtype=object)
+        out[ok] = [int(x) for x in vec[idx[ok]]]
+        return out
+
+    def _prod(self, rel, msgs, skip=None):
+        n = self.keys[rel][0].shape[0]
+        p = np.ones(n, dtype=object)
+        for c in self.children[rel]:
+            if c != skip:
+                p = p * self._at(rel, c, msgs)
+        return p
+
+    @staticmethod
+    def _u64(vals):
+        return np.array([min(int(v), SAT) for v in vals], dtype=np.uint64)
+
+    def shard_up(self, rel, msgs, lo, length):
+        w = self._prod(rel, msgs)
+        if self.parent[rel] < 0:
+            return self._u64([sum(w)])
+        out = [0] * length
+        for k, x in zip((self.col(rel, self.sep[rel]) - lo).tolist(), w.tolist()):
+            out[k] += x
+        return self._u64(out)
+
+    def shard_down(self, rel, down, msgs):
+        n = self.keys[rel][0].shape[0]
+        if down is None:
+            d = np.ones(n, dtype=object)
+        else:
+            vec, lo = down
+            d = np.array([int(vec[k - lo]) for k in self.col(rel, self.sep[rel]).tolist()], dtype=object)
+        parts = {}
+        for c in self.children[rel]:
+            x = d * self._prod(rel, msgs, skip=c)
+            vec, lo = msgs[c]
+            out = [0] * vec.shape[0]
+            for k, v in zip((self.col(rel, self.sep[c]) - lo).tolist(), x.tolist()):
+                if 0 <= k < len(out):
+                    out[k] += v
+            parts[c] = self._u64(out)
+        m = d * self._prod(rel, msgs)
+        keys = np.stack(self.keys[rel], axis=1) if n else np.zeros((0, len(self.keys[rel])), np.int64)
+        uk, inv = np.unique(keys, axis=0, return_inverse=True) if n else (keys, np.zeros(0, np.int64))
+        mult = [0] * uk.shape[0]
+        for i, v in zip(inv.reshape(-1).tolist(), m.tolist()):
+            mult[i] += v
+        self.local_keys[rel] = uk
+        return parts, self._u64(mult)
+
+
+def _sharded_query(seed):
+    from paper_2206_10435_gb300 import datagen as G
+    # a chain and a star-shaped tree (a relation with two children)
+    if seed % 2:
+        return G.chain3_uniform(seed=seed, rows=400, end_domain=60, mid_domain=12)
+    q = G.chain3_uniform(seed=seed, rows=300, end_domain=40, mid_domain=10)
+    R = q.relations
+    extra = G.Relation("R4", [R[0].attrs[1], 99], [R[1].keys[0][::-1].copy(), R[2].keys[1].copy()], [])
+    return G.Query("tree", R + [extra], q.attr_names)
+
+
+def _rank_sharded(rank, world, port, out, seed):
+    dist = _init(rank, world, port)
+    from paper_2206_10435_gb300 import shard as S
+    q = _sharded_query(seed)
+    eng = NumpyShard(q, rank, world)
+    total, up, down, mult = S.sharded_summary(dist, eng, eng.parent)
+    local = {t: [(tuple(int(x) for x in k), int(m)) for k, m in zip(eng.local_keys[t], mult[t])]
+             for t in mult}
+    out.put((rank, total, local))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_two_gloo_ranks_row_sharded_counting_matches_the_oracle(seed):
+    """Every relation split by rows over two ranks: the total and every key
+    tuple's multiplicity (summed over the ranks' local groups) equal the
+    oracle's counting pass on the whole relations."""
+    from oracle import oracle as O
+    res = _spawn(_rank_sharded, 2, seed)
+    q = _sharded_query(seed)
+    c = O.count(q, rows=True)
+    assert res[0][1] == res[1][1] == int(c.total) > 0
+    want = O.group_mult_from_counts(q, c)
+    for t, (allk, m) in enumerate(want):
+        got = {}
+        for _, _, local in res:
+            for k, v in local[t]:
+                got[k] = got.get(k, 0) + v
+        ref = {tuple(int(x) for x in k): int(v) for k, v in zip(allk, m)}
+        assert {k: v for k, v in got.items() if v} == {k: v for k, v in ref.items() if v}, t
