@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--slots", type=int, default=16)
     p.add_argument("--pool", type=int, default=512, help="serve workload: distinct small queries")
     p.add_argument("--serve-engine", default="native", choices=["native", "python"])
+    p.add_argument("--serve-chunk-log2", type=int, default=20,
+                   help="serve workload: rows per streamed chunk, log2")
     p.add_argument("--serve-max-rows", type=int, default=1 << 24,
                    help="serve workload: result rows streamed per request, in 2^20-row chunks "
                         "(0: the whole result)")
@@ -614,15 +616,15 @@ def run_serve(a, rank, world, local):
                  else small_ids[int(rng.integers(0, len(small_ids)))] for _ in range(n)]
         offsets = poisson_arrivals(rate, n, seed=int(rate) + (1000 + w if warm else 0))
         if a.serve_engine == "native":
-            srv = gj.NativeServer(ctx, n_slots=a.slots, hbm_budget=150 * 10**9, chunk_rows=1 << 20,
-                                  max_rows=a.serve_max_rows)
+            srv = gj.NativeServer(ctx, n_slots=a.slots, hbm_budget=150 * 10**9,
+                                  chunk_rows=1 << a.serve_chunk_log2, max_rows=a.serve_max_rows)
             res, sst = srv.run(picks, offsets)
             srv.close()
             st = native_latency_stats(res)
             st.update({"offered_qps": rate, "requests": n, "peak_in_flight": sst["peak_in_flight"],
                        "peak_admitted_gb": sst["peak_admitted_bytes"] / 1e9})
         else:
-            eng = GJEngine(ctx, a.slots, chunk_rows=1 << 20, max_rows=a.serve_max_rows)
+            eng = GJEngine(ctx, a.slots, chunk_rows=1 << a.serve_chunk_log2, max_rows=a.serve_max_rows)
             srv = Server(eng, n_slots=a.slots, hbm_budget=150 * 10**9)
             reqs = run_stream(srv, picks, offsets)
             st = latency_stats(reqs)
@@ -640,7 +642,7 @@ def run_serve(a, rank, world, local):
                                    f"each; {a.pool} queries of the batch distribution + 1% "
                                    "4-table chains of 1e7 rows (Zipf 1.1 over 1e6); summary + "
                                    f"the result's first {a.serve_max_rows or 'all'} rows streamed "
-                                   "in 2^20-row chunks per request; 150 GB HBM budget"),
+                                   f"in 2^{a.serve_chunk_log2}-row chunks per request; 150 GB HBM budget"),
                       "slots": a.slots, "engine": a.serve_engine, "factor_build_s": warm_s,
                       "l2": "not flushed: the requests of a stream share L2, as in service"},
            "sweep": sweep, "clocks": clk}

@@ -319,18 +319,23 @@ gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
  *
  * gj_batch_create plans queries q = 0..n_queries-1, query q being the
  * relations rel_ids[query_off[q] .. query_off[q+1]) (root first, same tree
- * rules as gj_query_create).  Restrictions: one or two key columns per
- * relation, one shared attribute between a relation and its parent, at most
- * 4 children per relation, at most 2^32 - 1 rows in all.  Planning reads the
- * key ranges (one synchronisation) and allocates the workspace; relations
- * must stay loaded and unchanged while the batch lives.
+ * rules as gj_query_create).  The batched kernels take queries whose
+ * relations have one or two key columns and share one attribute with their
+ * parent (at most 2^32 - 1 rows in all); any other acyclic query (three or
+ * more key columns, separators of several attributes) is planned as a single
+ * query and summarised by gj_batch_run after the batched kernels, writing
+ * its slot of the same arrays.  Planning reads the key ranges (one
+ * synchronisation) and allocates the workspace; relations must stay loaded
+ * and unchanged while the batch lives.
  *
  * gj_batch_run enqueues the whole summary on the context's stream without
  * any synchronisation and writes |Q| (UINT64_MAX on overflow) to
  * totals_dev[q] and GJ_OK / GJ_ERR_OVERFLOW to status_dev[q] (may be NULL).
  * With use_graph != 0 the sequence is captured into a CUDA graph on the
  * first call (and again when the outputs or parameters change) and each
- * call is one graph launch.
+ * call is one graph launch.  Queries planned as single queries run outside
+ * the graph, on the same stream after it, and the call then waits for the
+ * stream.
  */
 typedef struct gj_batch gj_batch;
 #define GJ_BATCH_GRID_MULT 1   /* persistent grids = SMs x this (1..64, default 4) */

@@ -32,6 +32,14 @@ Readings of the paper that this oracle fixes:
   definition: every row combination agreeing on all shared attributes) is
   computed by sort-based equi-joins R0 |><| R1 on B, then with R2 on (C, A),
   and put in canonical order by a sort.
+* Any other query whose relation order gives no join tree (Sections 3.2.1
+  and 3.4 answer it over a junction tree): when every relation after the
+  first shares an attribute with the relations before it, V is the
+  attributes in order of first appearance (relation 0's columns in declared
+  order, then each relation's new attributes in declared column order); the
+  result is again every row combination agreeing on all shared attributes,
+  built by a cascade of sort-based equi-joins, relation j joined on every
+  attribute it shares with relations 0..j-1, then sorted canonically.
 * Early projection (Section 3.7): a dropped attribute is deleted from V.
   The result is the same bag of row-id tuples, its columns are the
   remaining V attributes and the payloads, and its rows are ordered by the
@@ -107,7 +115,8 @@ class Plan:
     V: list            # attribute ids in summary-column order
     var_rel: list      # relation that introduces V[i]
     var_col: list      # its column there
-    cyclic: bool = False   # the 3-cycle R0(A,B), R1(B,C), R2(C,A)
+    cyclic: bool = False   # no join tree: the 3-cycle, or a general cyclic query
+    kind: str = "tree"     # "tree", "triangle" (R0(A,B), R1(B,C), R2(C,A)) or "cyclic"
 
 
 def _triangle(rels):
@@ -130,7 +139,7 @@ def plan(query, drop=()) -> Plan:
     if tri:
         ab, bc, ca = tri
         return Plan([-1, 0, 1], [[], [ab], [bc, ca]], [0, 1, 2], list(rels[0].attrs) + [bc],
-                    [0, 0, 1], [0, 1, rels[1].attrs.index(bc)], cyclic=True)
+                    [0, 0, 1], [0, 1, rels[1].attrs.index(bc)], cyclic=True, kind="triangle")
     drop = set(drop)
     for a in drop:
         if sum(R.attrs.count(a) for R in rels) != 1:
@@ -144,7 +153,9 @@ def plan(query, drop=()) -> Plan:
             raise NotAcyclic(f"relation {j} shares no attribute with relations before it")
         p = next((i for i in range(j) if set(shared) <= set(rels[i].attrs)), None)
         if p is None:
-            raise NotAcyclic(f"relation {j}: no earlier relation holds all of {shared}")
+            if drop:
+                raise NotAcyclic(f"relation {j}: no earlier relation holds all of {shared}")
+            return cyclic_plan(query)
         parent.append(p)
         sep.append(shared)
         seen.update(rels[j].attrs)
@@ -162,6 +173,61 @@ def plan(query, drop=()) -> Plan:
                 var_rel.append(t)
                 var_col.append(c)
     return Plan(parent, sep, order, V, var_rel, var_col)
+
+
+def cyclic_plan(query) -> Plan:
+    """The plan of a query whose relation order gives no join tree: V by
+    first appearance; sep[j] = every attribute relation j shares with
+    relations 0..j-1 (it must share one); parent[j] = the first earlier
+    relation sharing one of them."""
+    rels = query.relations
+    parent, sep, seen = [-1], [[]], set(rels[0].attrs) if rels else set()
+    for j in range(1, len(rels)):
+        shared = [a for a in rels[j].attrs if a in seen]
+        if not shared:
+            raise NotAcyclic(f"relation {j} shares no attribute with relations before it")
+        parent.append(next(i for i in range(j) if set(shared) & set(rels[i].attrs)))
+        sep.append(shared)
+        seen.update(rels[j].attrs)
+    V, var_rel, var_col = [], [], []
+    for t, R in enumerate(rels):
+        for c, a in enumerate(R.attrs):
+            if a not in V:
+                V.append(a)
+                var_rel.append(t)
+                var_col.append(c)
+    return Plan(parent, sep, list(range(len(rels))), V, var_rel, var_col, cyclic=True, kind="cyclic")
+
+
+def _cyclic_rowids(query, pl) -> np.ndarray:
+    """Row-id tuples of a query by the plain definition (every combination
+    of rows agreeing on all shared attributes), in canonical order: a
+    cascade of sort-based equi-joins, relation j joined on all the
+    attributes it shares with relations 0..j-1, then one sort."""
+    rels = query.relations
+    col = lambda R, a: np.asarray(R.keys[R.attrs.index(a)], dtype=np.int64)
+    t = np.arange(rels[0].n_rows, dtype=np.int64).reshape(-1, 1)
+    holder = {a: 0 for a in rels[0].attrs}          # first relation holding an attribute
+    for j in range(1, len(rels)):
+        R = rels[j]
+        shared = pl.sep[j]
+        left = np.stack([col(rels[holder[a]], a)[t[:, holder[a]]] for a in shared], axis=1)
+        right = np.stack([col(R, a) for a in shared], axis=1)
+        # shared-value tuples of both sides numbered alike, then one equi-join
+        both = np.concatenate([left, right]) if left.shape[0] + right.shape[0] else left
+        if both.shape[0]:
+            _, ids = np.unique(both, axis=0, return_inverse=True)
+            ids = ids.reshape(-1)
+        else:
+            ids = np.zeros(0, np.int64)
+        li, ri = _equi_join(ids[:left.shape[0]], ids[left.shape[0]:])
+        t = np.concatenate([t[li], ri.reshape(-1, 1)], axis=1)
+        for a in R.attrs:
+            holder.setdefault(a, j)
+    keys = [t[:, c] for c in reversed(range(t.shape[1]))]
+    keys += [col(rels[r], a)[t[:, r]] for r, a in zip(reversed(pl.var_rel), reversed(pl.V))]
+    order = np.lexsort(keys) if t.shape[0] else np.zeros(0, np.int64)
+    return t[order].astype(np.int32)
 
 
 class _Marshal:
@@ -248,7 +314,8 @@ def count(query, rows: bool = False) -> Counts:
     if pl.cyclic:
         if rows:
             raise NotImplementedError("per-row multiplicities of the cyclic join")
-        return Counts(int(_triangle_rowids(query, pl).shape[0]), False)
+        t = _triangle_rowids(query, pl) if pl.kind == "triangle" else _cyclic_rowids(query, pl)
+        return Counts(int(t.shape[0]), False)
     lib = _load()
     m = _Marshal(query, pl)
     k = len(query.relations)
@@ -281,7 +348,7 @@ def join(query, max_tuples: int = 50_000_000, drop=()) -> Joined:
     V of the projection when attributes are dropped)."""
     pl = plan(query, drop)
     if pl.cyclic:
-        t = _triangle_rowids(query, pl)
+        t = _triangle_rowids(query, pl) if pl.kind == "triangle" else _cyclic_rowids(query, pl)
         if t.shape[0] > max_tuples:
             raise ValueError(f"join result too large to materialise ({t.shape[0]} tuples)")
         return Joined(t, [])

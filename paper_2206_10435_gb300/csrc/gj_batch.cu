@@ -27,8 +27,12 @@
 //                          aggregated across each warp's runs of equal target
 //   totals                 |Q| and status per query
 //
-// Restrictions of this path: every relation has one or two key columns and
-// every non-root relation shares exactly one attribute with its parent.
+// The batched kernels take relations of one or two key columns whose
+// non-root relations share exactly one attribute with their parent.  Other
+// queries of a batch (three or more key columns, separators of several
+// attributes) are summarised through the single-query path by gj_batch_run,
+// after the batched kernels, and report their totals and statuses in the
+// same arrays.
 #include <string.h>
 
 #include <algorithm>
@@ -49,7 +53,7 @@ gj_status check_device_error(Ctx &c);
 namespace {
 
 constexpr int BT = 256;
-constexpr int BMAXCH = 4;                 // children per relation in a batch
+constexpr int BMAXCH = MAX_REL;           // children per relation in a batch
 constexpr int64_t PACK_TILE = 4096;
 
 // per batch relation, device side
@@ -302,11 +306,17 @@ struct BatchState {
     // the legacy default stream, which cannot be captured) and launched on
     // the context's stream
     cudaStream_t capture_stream = nullptr;
+    // queries outside the batched kernels' shapes: (query index, its query)
+    std::vector<std::pair<int, gj_query *>> fallback;
+    std::vector<uint64_t> fb_total;
+    std::vector<int32_t> fb_status;
 };
 
 namespace {
 
 void batch_free(BatchState &b) {
+    for (auto &f : b.fallback) gj_query_destroy(f.second);
+    b.fallback.clear();
     Ctx &c = b.cs->c;
     if (b.exec) cudaGraphExecDestroy(b.exec);
     if (b.graph) cudaGraphDestroy(b.graph);
@@ -392,24 +402,26 @@ gj_status gj_batch_create(gj_ctx *ctx, const int32_t *rel_ids, const int32_t *qu
     std::vector<HRel> hr;
     std::vector<int> qroot(n_queries);
     gj_status st = GJ_OK;
+    std::vector<std::pair<int, gj_query *>> fallback;
     for (int q = 0; q < n_queries && st == GJ_OK; q++) {
         int k = query_off[q + 1] - query_off[q];
         if (k < 1 || k > MAX_REL) { st = GJ_ERR_INVALID; break; }
         int base = (int)hr.size();
         qroot[q] = base;
         std::vector<int32_t> seen;
+        bool other_shape = false;   // outside the batched kernels' shapes
         for (int j = 0; j < k; j++) {
             auto it = cs.rels.find(rel_ids[query_off[q] + j]);
             if (it == cs.rels.end()) { st = GJ_ERR_INVALID; break; }
             Relation *R = it->second.get();
-            if (R->nk < 1 || R->nk > 2) { st = GJ_ERR_INVALID; break; }
+            if (R->nk < 1 || R->nk > 2) { other_shape = true; break; }
             HRel h{R, q, j, -1, 0, 0, R->nk == 2 ? 1 : -1, {}, {}};
             if (j > 0) {
                 std::vector<int> shared_cols;
                 for (int cc = 0; cc < R->nk; cc++)
                     if (std::find(seen.begin(), seen.end(), R->attr[cc]) != seen.end())
                         shared_cols.push_back(cc);
-                if (shared_cols.size() != 1) { st = GJ_ERR_INVALID; break; }
+                if (shared_cols.size() != 1) { other_shape = true; break; }
                 int32_t a = R->attr[shared_cols[0]];
                 int parent = -1;
                 for (int i = 0; i < j && parent < 0; i++) {
@@ -422,7 +434,7 @@ gj_status gj_batch_create(gj_ctx *ctx, const int32_t *rel_ids, const int32_t *qu
                 h.col_a = shared_cols[0];
                 h.col_b = R->nk == 2 ? 1 - shared_cols[0] : -1;
                 HRel &P = hr[base + parent];
-                if ((int)P.children.size() >= BMAXCH) { st = GJ_ERR_INVALID; break; }
+                if ((int)P.children.size() >= BMAXCH) { other_shape = true; break; }
                 int pc = P.R->attr[P.col_a] == a ? 0 : 1;
                 P.children.push_back(base + j);
                 P.child_pcol.push_back(pc);
@@ -430,8 +442,20 @@ gj_status gj_batch_create(gj_ctx *ctx, const int32_t *rel_ids, const int32_t *qu
             for (int32_t a : R->attr) seen.push_back(a);
             hr.push_back(h);
         }
+        if (st == GJ_OK && other_shape) {
+            // this query goes through the single-query path: planned (and
+            // its factors built) now, summarised by gj_batch_run
+            hr.resize(base);
+            gj_query *fq = nullptr;
+            st = gj_query_create(ctx, rel_ids + query_off[q], k, &fq);
+            if (st == GJ_OK) fallback.emplace_back(q, fq);
+        }
     }
-    if (st != GJ_OK) { if (dev_prev != c.device) cudaSetDevice(dev_prev); return st; }
+    auto drop_fallback = [&]() {
+        for (auto &f : fallback) gj_query_destroy(f.second);
+        fallback.clear();
+    };
+    if (st != GJ_OK) { drop_fallback(); if (dev_prev != c.device) cudaSetDevice(dev_prev); return st; }
     // renumber: deepest level first, then query, then position
     const int Rn = (int)hr.size();
     int levels = 0;
@@ -447,6 +471,13 @@ gj_status gj_batch_create(gj_ctx *ctx, const int32_t *rel_ids, const int32_t *qu
     b.Q = n_queries;
     b.R = Rn;
     b.levels = levels;
+    b.fallback = fallback;
+    fallback.clear();
+    if (Rn == 0) {   // every query takes the single-query path
+        if (dev_prev != c.device) cudaSetDevice(dev_prev);
+        *out = bb.release();
+        return GJ_OK;
+    }
     b.lr_beg.assign(levels, 0);
     b.lr_end.assign(levels, 0);
     for (int d = 0; d < levels; d++) {
@@ -596,7 +627,9 @@ gj_status gj_batch_run(gj_batch *batch, int32_t use_graph, uint64_t *totals_dev,
     cudaGetDevice(&dev_prev);
     if (dev_prev != c.device) cudaSetDevice(c.device);
     cudaError_t e = cudaSuccess;
-    if (!use_graph) {
+    if (b.R == 0) {
+        // nothing for the batched kernels
+    } else if (!use_graph) {
         e = batch_enqueue(b, c, totals_dev, status_dev);
     } else {
         if (b.exec && (b.g_totals != totals_dev || b.g_status != status_dev || b.g_mult != b.grid_mult)) {
@@ -626,13 +659,34 @@ gj_status gj_batch_run(gj_batch *batch, int32_t use_graph, uint64_t *totals_dev,
         if (e == cudaSuccess) e = cudaGraphLaunch(b.exec, c.stream);
         if (e == cudaSuccess) c.launches += b.g_launches;
     }
+    // the other queries, one by one on the same stream (after the batched
+    // kernels, which also write their slots), their results copied in
+    gj_status st = GJ_OK;
+    if (e == cudaSuccess && !b.fallback.empty()) {
+        b.fb_total.assign(b.fallback.size(), 0);
+        b.fb_status.assign(b.fallback.size(), GJ_OK);
+        for (size_t i = 0; i < b.fallback.size() && st == GJ_OK; i++) {
+            uint64_t t = 0;
+            gj_status s1 = gj_summarize(b.fallback[i].second, &t);
+            if (s1 != GJ_OK && s1 != GJ_ERR_OVERFLOW) { st = s1; break; }
+            b.fb_total[i] = s1 == GJ_ERR_OVERFLOW ? SAT : t;
+            b.fb_status[i] = s1;
+        }
+        for (size_t i = 0; i < b.fallback.size() && st == GJ_OK && e == cudaSuccess; i++) {
+            const int q = b.fallback[i].first;
+            e = cudaMemcpyAsync(totals_dev + q, &b.fb_total[i], 8, cudaMemcpyHostToDevice, c.stream);
+            if (e == cudaSuccess && status_dev)
+                e = cudaMemcpyAsync(status_dev + q, &b.fb_status[i], 4, cudaMemcpyHostToDevice, c.stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);   // the host values are read by then
+    }
     if (dev_prev != c.device) cudaSetDevice(dev_prev);
     if (e != cudaSuccess) {
         note_cuda_error(e, __FILE__, __LINE__);
         cudaGetLastError();
         return GJ_ERR_CUDA;
     }
-    return GJ_OK;
+    return st;
 }
 
 void gj_batch_destroy(gj_batch *batch) {

@@ -170,11 +170,6 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
                const uint32_t *__restrict__ lo_in, const uint64_t *__restrict__ unit_in,
                ExpandOut o) {
     __shared__ uint32_t s_off[EXP_TILE + 1];
-    // the tile's items, staged by coalesced loads: first row, rows per way,
-    // first live group in the segment, product of the counts so far
-    __shared__ uint64_t s_iA[EXP_TILE + 1];
-    __shared__ uint64_t s_iu[EXP_TILE + 1];
-    __shared__ uint32_t s_ilo[EXP_TILE + 1];
     __shared__ uint64_t s_A[EXP_TILE];   // tile map only: first rows of the tile's blocks
     __shared__ uint64_t s_end;            // and the end of its last block
     const int64_t F = *F_dev, Fout = *Fout_dev;
@@ -192,21 +187,16 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
             return;
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < nitems; t += DT) {
-            s_off[t] = excl[first + t];
-            s_iA[t] = s.A[first + t];
-            s_iu[t] = unit_in[first + t];
-            s_ilo[t] = lo_in[first + t];
-        }
+        for (int t = threadIdx.x; t < nitems; t += DT) s_off[t] = excl[first + t];
         __syncthreads();
         for (int64_t slot = o0 + threadIdx.x; slot < o1; slot += DT) {
             int a = 0, b = nitems;   // last t with s_off[t] <= slot
             while (a < b) { int m = (a + b) >> 1; if (s_off[m] <= (uint32_t)slot) a = m + 1; else b = m; }
             const int64_t i = first + a - 1;
-            const uint32_t h = s_ilo[a - 1] + (uint32_t)(slot - s_off[a - 1]);
+            const uint32_t h = lo_in[i] + (uint32_t)(slot - s_off[a - 1]);
             const uint32_t g = s.lgid[h];
-            const uint64_t unit = s_iu[a - 1];
-            const uint64_t A = s_iA[a - 1] + unit * s.loff[h];
+            const uint64_t unit = unit_in[i];
+            const uint64_t A = s.A[i] + unit * s.loff[h];
             o.A[slot] = A;
             if (o.W) o.W[slot] = s.W[i] * (uint64_t)(s.gstart[g + 1] - s.gstart[g]);
             if (o.tile_first) {

@@ -43,13 +43,22 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     return x;
 }
 
-__global__ void k_chunk_hash(const void *col, int width, int col_idx, uint64_t row0, int64_t n,
-                             unsigned long long *h) {
+// every column of a chunk in one launch (blockIdx.y = column)
+struct ChunkCols {
+    int n;
+    const void *col[64];
+    int width[64];
+};
+
+__global__ void k_chunk_hash(ChunkCols cc, uint64_t row0, int64_t n, unsigned long long *h) {
+    const int c = blockIdx.y;
+    const void *col = cc.col[c];
+    const int width = cc.width[c];
     uint64_t acc = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint64_t v = width == 8 ? ((const uint64_t *)col)[i] : (uint64_t)((const uint32_t *)col)[i];
-        acc ^= mix64(v ^ mix64(((uint64_t)col_idx << 40) ^ (row0 + (uint64_t)i)));
+        acc ^= mix64(v ^ mix64(((uint64_t)c << 40) ^ (row0 + (uint64_t)i)));
     }
     for (int d = 16; d; d >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, d);
     if ((threadIdx.x & 31) == 0 && acc) atomicXor(h, (unsigned long long)acc);
@@ -143,11 +152,13 @@ void run_one(ServerState &S, int slot, Pending &p) {
             uint64_t n = 0;
             st = desummarize(qs, done, std::min<uint64_t>(S.chunk, want - done), bufs.data(), nullptr, &n);
             if (st != GJ_OK || n == 0) break;
-            for (size_t i = 0; i < widths.size(); i++) {
-                int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n, 256), c.num_sms * 4));
-                k_chunk_hash<<<grid, 256, 0, c.stream>>>(bufs[i], widths[i], (int)i, done, (int64_t)n,
-                                                          S.hash[slot]);
-            }
+            ChunkCols cc{};
+            cc.n = (int)widths.size();
+            for (int i = 0; i < cc.n && i < 64; i++) { cc.col[i] = bufs[i]; cc.width[i] = widths[i]; }
+            const int cols = std::min(cc.n, 64);
+            const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)n, 256),
+                                                                      std::max<int64_t>(1, c.num_sms * 4 / cols)));
+            k_chunk_hash<<<dim3(gx, cols), 256, 0, c.stream>>>(cc, done, (int64_t)n, S.hash[slot]);
             if (done == 0) r.t_chunk = now_s();   // the first chunk is out (desummarise waited for it)
             done += n;
         }

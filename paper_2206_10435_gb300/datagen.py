@@ -156,6 +156,36 @@ def triangle_query(seed: int, rows, domain: int, s: float = 0.0, payload_dtype=n
     return Query(name, rels, {0: "A", 1: "B", 2: "C"})
 
 
+# Attribute lists of cyclic query shapes (relations in order; a relation's
+# keys are these attributes in this declared order).
+CYCLIC_SHAPES = {
+    "square": [(0, 1), (1, 2), (2, 3), (3, 0)],                       # 4-cycle
+    "pentagon": [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0)],             # 5-cycle
+    "bowtie": [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4), (4, 2)],       # two triangles on C
+    "diamond": [(0, 1), (1, 2), (2, 0), (2, 3), (3, 0)],              # triangles sharing A-C
+    "k4": [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2), (1, 3)],           # every pair of 4 attributes
+    "wide": [(0, 1, 2), (2, 3), (3, 1, 0)],                           # relations with three keys
+    "pendant": [(0, 1), (1, 2), (2, 3), (3, 0), (3, 5)],              # 4-cycle and a leaf
+}
+
+
+def cyclic_query(seed: int, shape: str, rows, domain: int, s: float = 0.0,
+                 payload_dtype=np.int64) -> Query:
+    """A query of one of CYCLIC_SHAPES: rows[i] rows per relation (an int
+    gives every relation that many), keys Zipf(s) over [0, domain) (uniform
+    for s = 0), one payload per relation (none if payload_dtype is None)."""
+    rng = np.random.default_rng(seed)
+    attrs = CYCLIC_SHAPES[shape]
+    rows = [rows] * len(attrs) if isinstance(rows, (int, np.integer)) else list(rows)
+    rels = []
+    for i, at in enumerate(attrs):
+        n = int(rows[i])
+        cols = [zipf_keys(rng, n, s, domain) for _ in at]
+        pays = [_payload(rng, n, payload_dtype)] if payload_dtype is not None else []
+        rels.append(Relation(f"R{i}", list(at), cols, pays))
+    return Query(shape, rels, {a: "ABCDEF"[a] for at in attrs for a in at})
+
+
 def star_poisson(seed: int = SEED_BASE + 2, fact_rows: int = 10**8, domain: int = 10**6,
                  n_dims: int = 4, lam: float = 2.0) -> Query:
     """Fact F(K_1..K_n, P) with K_j uniform over [0, domain), joined to

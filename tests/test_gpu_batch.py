@@ -100,11 +100,74 @@ def test_batch_grid_sizes_agree(ctx):
             ctx.release_relation(r)
 
 
-def test_batch_rejects_unsupported_shapes(ctx):
+def _other_shape_queries():
+    """Queries outside the batched kernels' shapes: three-key relations, a
+    separator of two attributes, a relation with six children."""
+    rng = np.random.default_rng(12)
+    r = lambda n, d: rng.integers(0, d, n, dtype=np.int32)
+    qs = []
+    # a three-key root with two children
+    qs.append(G.Query("three", [G.Relation("F", [0, 1, 2], [r(300, 6), r(300, 5), r(300, 7)]),
+                                G.Relation("A", [0, 3], [r(40, 6), r(40, 4)]),
+                                G.Relation("B", [2], [r(30, 7)])]))
+    # a child joined on two attributes
+    qs.append(G.Query("twosep", [G.Relation("P", [0, 1], [r(200, 4), r(200, 5)]),
+                                 G.Relation("C", [0, 1, 2], [r(150, 4), r(150, 5), r(150, 9)]),
+                                 G.Relation("D", [2], [r(20, 9)])]))
+    # six children of one relation (the batched kernels take up to 16)
+    qs.append(G.Query("six", [G.Relation("H", [0], [r(50, 8)])] +
+                      [G.Relation(f"K{i}", [0, 10 + i], [r(30, 8), r(30, 3)]) for i in range(6)]))
+    # three-key relations all through a chain
+    qs.append(G.Query("wide3", [G.Relation("X", [0, 1, 2], [r(100, 3), r(100, 3), r(100, 4)]),
+                                G.Relation("Y", [2, 3, 4], [r(100, 4), r(100, 3), r(100, 3)])]))
+    return qs
+
+
+def test_batch_takes_every_acyclic_shape(ctx):
+    """Chains the batched kernels take, mixed with queries they do not (the
+    batch summarises those through the single-query path): every total and
+    status equals the oracle's, with and without the graph, and a batch of
+    only such queries works too."""
+    from paper_2206_10435_gb300 import gj
+    others = _other_shape_queries()
+    queries = G.batch_queries(seed=44, n_queries=30, rows_range=(1, 2000), domain_range=(2, 300))
+    mixed = []
+    for i, q in enumerate(queries):
+        mixed.append(q)
+        if i % 8 == 3:
+            mixed.append(others[(i // 8) % len(others)])
+    mixed += others
+    for qs in (mixed, others):
+        ids = _load(ctx, qs)
+        ref = [O.count(q) for q in qs]
+        b = gj.Batch(ctx, ids)
+        # the six-children query is batched; the others take the single-query path
+        single = [o for o in others if o.name != "six"]
+        batched = [q for q in qs if all(q is not o for o in single)]
+        assert b.n_relations == sum(len(q.relations) for q in batched)
+        for use_graph in (False, True, True):
+            b.run(use_graph=use_graph)
+            torch.cuda.synchronize()
+            tot = b.totals.cpu().numpy().view(np.uint64)
+            st = b.status.cpu().numpy()
+            for j, c in enumerate(ref):
+                assert int(tot[j]) == (CAP if c.overflow else c.total), (j, qs[j].name)
+                assert st[j] == (gj.GJ_ERR_OVERFLOW if c.overflow else gj.GJ_OK), j
+        b.close()
+        for q in ids:
+            for x in q:
+                ctx.release_relation(x)
+
+
+def test_batch_rejects_a_cyclic_query(ctx):
     from paper_2206_10435_gb300 import gj
     a = torch.tensor([0, 1], dtype=torch.int32, device="cuda")
-    r3 = ctx.load_relation([a, a, a], [0, 1, 2])
+    r0 = ctx.load_relation([a, a], [0, 1])
+    r1 = ctx.load_relation([a, a], [1, 2])
+    r2 = ctx.load_relation([a, a], [2, 3])
+    r3 = ctx.load_relation([a, a], [3, 0])
     with pytest.raises(gj.GJError) as e:
-        gj.Batch(ctx, [[r3]])
-    assert e.value.status == gj.GJ_ERR_INVALID
-    ctx.release_relation(r3)
+        gj.Batch(ctx, [[r0, r1, r2, r3]])
+    assert e.value.status == gj.GJ_ERR_NOT_ACYCLIC
+    for r in (r0, r1, r2, r3):
+        ctx.release_relation(r)

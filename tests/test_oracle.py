@@ -343,17 +343,101 @@ def test_cyclic_triangle_complete_tripartite_closed_form():
     assert j.rowids.shape[0] == na * nb * nc * mr * ms * mt
 
 
-def test_other_cyclic_queries_are_rejected():
-    # a 4-cycle, and a triangle one of whose relations holds a third key:
-    # neither is a join tree nor the supported 3-cycle
+def tiny_cyclic():
+    qs = []
+    shapes = list(G.CYCLIC_SHAPES)
+    for seed in range(70):
+        shape = shapes[seed % len(shapes)]
+        k = len(G.CYCLIC_SHAPES[shape])
+        rows = [1 + (seed + 2 * i) % (4 if k <= 5 else 3) for i in range(k)]
+        q = G.cyclic_query(7500 + seed, shape, rows, domain=2 + (seed // 7) % 2,
+                           payload_dtype=np.int32 if seed % 2 else np.int64)
+        if seed % 3 == 1:   # a relation's columns in another declared order
+            r = seed % k
+            R = q.relations[r]
+            q.relations[r] = G.Relation(R.name, R.attrs[::-1], R.keys[::-1], R.payloads)
+        qs.append(q)
+    return qs
+
+
+def first_appearance(q):
+    V = []
+    for R in q.relations:
+        for a in R.attrs:
+            if a not in V:
+                V.append(a)
+    return V
+
+
+@pytest.mark.parametrize("q", tiny_cyclic(), ids=lambda q: f"{q.name}{id(q) % 997}")
+def test_cyclic_queries_match_nested_loops(q):
+    """Queries whose relation order gives no join tree (4- and 5-cycles, two
+    triangles, all pairs of four attributes, three-key relations, a cycle
+    with a leaf): every row combination agreeing on all shared attributes,
+    ordered by V (attributes by first appearance), then the row ids; the
+    columns and the GFJS levels by their definitions."""
+    pl = O.plan(q)
+    assert pl.cyclic and pl.kind == "cyclic"
+    assert pl.V == first_appearance(q)
+    bf = canonical(q, brute_force(q), pl.V)
+    assert O.count(q).total == len(bf)
+    j = O.join(q)
+    assert [tuple(t) for t in j.rowids.tolist()] == [tuple(t) for t in bf]
+    cols = O.columns(q, j.rowids)
+    for i, t in enumerate(bf[:40]):
+        assert [int(cols[v][i]) for v in range(len(pl.V))] == [value_of(q, t, a) for a in pl.V]
+    lv = O.gfjs_levels(q, j.rowids)
+    ref = levels_by_definition(q, bf, pl.V)
+    for l in range(len(pl.V)):
+        assert [list(x) for x in zip(lv[l].value.tolist(), lv[l].freq.tolist(),
+                                     lv[l].offset.tolist())] == ref[l]
+
+
+@pytest.mark.parametrize("shape,seed,s", [("square", 0, 0.0), ("square", 1, 1.2), ("pentagon", 2, 0.7),
+                                          ("pentagon", 3, 0.0)])
+def test_cycle_size_is_the_trace_of_the_count_matrices(shape, seed, s):
+    # an L-cycle R_i(A_i, A_i+1 mod L): |Q| = sum over (a_0..a_L-1) of
+    # prod_i n_i(a_i, a_i+1) = trace(M_0 ... M_L-1), M_i the pair-count
+    # matrices: a library matrix product, independent of the oracle's joins
+    d = 9 + seed
+    q = G.cyclic_query(9200 + seed, shape, [200 + 37 * i for i in range(5)][:len(G.CYCLIC_SHAPES[shape])],
+                       domain=d, s=s)
+    P = np.eye(d, dtype=np.int64)
+    for R in q.relations:
+        m = np.zeros((d, d), np.int64)
+        np.add.at(m, (R.keys[0].astype(np.int64), R.keys[1].astype(np.int64)), 1)
+        P = P @ m
+    assert O.count(q).total == int(np.trace(P))
+
+
+def test_cyclic_all_equal_keys_give_the_product():
+    for shape in G.CYCLIC_SHAPES:
+        rows = [2 + i for i in range(len(G.CYCLIC_SHAPES[shape]))]
+        q = G.cyclic_query(1, shape, rows, domain=1)
+        assert O.count(q).total == int(np.prod(rows)), shape
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_general_cyclic_path_equals_the_triangle_path(seed):
+    # the 3-cycle has its own path (two equi-joins); the general cascade,
+    # given the same query, gives the same rows in the same order
+    q = G.triangle_query(9300 + seed, [40, 50, 30], domain=4 + seed % 3, s=0.5 * (seed % 3))
+    pl = O.cyclic_plan(q)
+    assert pl.V == O.plan(q).V
+    assert np.array_equal(O._cyclic_rowids(q, pl), O.join(q).rowids)
+
+
+def test_queries_without_a_shared_attribute_are_rejected():
+    # a relation sharing no attribute with those before it makes a cross
+    # product, not an equi-join; early projection of a cyclic query is not
+    # supported
     a = np.array([0, 1], np.int32)
-    q4 = G.Query("square", [G.Relation("R", [0, 1], [a, a]), G.Relation("S", [1, 2], [a, a]),
-                            G.Relation("T", [2, 3], [a, a]), G.Relation("U", [3, 0], [a, a])])
-    q3 = G.Query("triangle3", [G.Relation("R", [0, 1, 4], [a, a, a]), G.Relation("S", [1, 2], [a, a]),
-                               G.Relation("T", [2, 0], [a, a])])
-    for q in (q4, q3):
-        with pytest.raises(O.NotAcyclic):
-            O.plan(q)
+    cross = G.Query("cross", [G.Relation("R", [0, 1], [a, a]), G.Relation("S", [2, 3], [a, a])])
+    with pytest.raises(O.NotAcyclic):
+        O.plan(cross)
+    sq = G.cyclic_query(2, "pendant", 4, domain=2)
+    with pytest.raises(O.NotAcyclic):
+        O.plan(sq, drop=[5])
 
 
 def test_plan_of_branching_tree():
