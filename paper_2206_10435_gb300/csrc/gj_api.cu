@@ -16,6 +16,7 @@ cudaError_t factor_build_many(Ctx &c, const std::vector<Relation *> &R, const st
 void factor_free(Ctx &c, Factor &F);
 void query_free_summary(Ctx &c, QueryState &q);
 gj_status summarize(QueryState &q, uint64_t *total_out);
+bool plan_cyclic(QueryState &q);
 gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
                       uint32_t *const *rowid_cols, uint64_t *n_out);
 gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, int32_t *val,
@@ -535,7 +536,24 @@ gj_status query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel,
                 for (int32_t a : shared) all &= std::find(pa.begin(), pa.end(), a) != pa.end();
                 if (all) parent = i;
             }
-            if (parent < 0) return GJ_ERR_NOT_ACYCLIC;
+            if (parent < 0) {
+                // no join tree in this order: a cyclic query, answered over
+                // one maxclique (gj_cyclic.cu), when every relation after the
+                // first shares an attribute with those before it
+                if (!drop.empty()) return GJ_ERR_NOT_ACYCLIC;
+                for (int i = 0; i < n_rel; i++) {
+                    auto ri = ctx->s.rels.find(rel_ids[i]);
+                    if (ri == ctx->s.rels.end()) return GJ_ERR_INVALID;
+                    q.r[i].rel_id = rel_ids[i];
+                    q.r[i].R = ri->second.get();
+                }
+                if (!plan_cyclic(q)) return GJ_ERR_NOT_ACYCLIC;
+                DeviceGuard g(ctx->s.c.device);
+                gj_status st = get_factors(ctx->s, q.r);
+                if (st != GJ_OK) return st;
+                *out = qq.release();
+                return GJ_OK;
+            }
             t.parent = parent;
             const std::vector<int32_t> &pa = q.r[parent].R->attr;
             for (int32_t a : shared)
@@ -663,7 +681,7 @@ gj_status gj_summarize(gj_query *q, uint64_t *total) {
 
 gj_status gj_summary_groups(gj_query *q, int32_t rel, uint64_t *w_dev, uint64_t *mult_dev,
                             uint64_t *off_dev) {
-    if (!q || rel < 0 || rel >= q->s.k || q->s.tri) return GJ_ERR_INVALID;
+    if (!q || rel < 0 || rel >= q->s.k || q->s.tri || q->s.cyc) return GJ_ERR_INVALID;
     if (!q->s.summarized && !q->s.overflow) return GJ_ERR_STATE;
     DeviceGuard g(q->s.cs->c.device);
     QRel &t = q->s.r[rel];

@@ -612,9 +612,13 @@ bool make_emit_spec(QueryState &q, void *const *out_cols, uint32_t *const *rowid
 gj_status tri_desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
                           uint32_t *const *rowid_cols, uint64_t *n_out);
 
+gj_status cyc_desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
+                          uint32_t *const *rowid_cols, uint64_t *n_out);
+
 gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const *out_cols,
                       uint32_t *const *rowid_cols, uint64_t *n_out) {
     if (q.tri) return tri_desummarize(q, row0, nrows, out_cols, rowid_cols, n_out);
+    if (q.cyc) return cyc_desummarize(q, row0, nrows, out_cols, rowid_cols, n_out);
     Ctx &c = q.ctx();
     *n_out = 0;
     if (!q.summarized) return GJ_ERR_STATE;
@@ -699,7 +703,7 @@ gj_status level_runs(QueryState &q, int level, uint64_t row0, uint64_t nrows, in
                      uint64_t *freq, uint64_t *off, uint64_t cap, uint64_t *n_out) {
     Ctx &c = q.ctx();
     *n_out = 0;
-    if (q.tri) return GJ_ERR_INVALID;   // the cyclic join's summary is its block list
+    if (q.tri || q.cyc) return GJ_ERR_INVALID;   // a cyclic join's summary is its block list
     if (!q.summarized) return GJ_ERR_STATE;
     if (q.overflow) return GJ_ERR_OVERFLOW;
     if (level < 0 || level >= (int)q.var_rel.size()) return GJ_ERR_INVALID;

@@ -117,7 +117,7 @@ using namespace gj;
 extern "C" {
 
 gj_status gj_summary_save(gj_query *qq, const char *path, uint64_t *bytes) {
-    if (!qq || !path || qq->s.tri) return GJ_ERR_INVALID;
+    if (!qq || !path || qq->s.tri || qq->s.cyc) return GJ_ERR_INVALID;
     QueryState &q = qq->s;
     if (!q.summarized) return GJ_ERR_STATE;
     Ctx &c = q.ctx();

@@ -86,6 +86,9 @@ struct ServerState {
     // lent to the queries the slot runs, so a request allocates nothing
     std::vector<std::unique_ptr<Ctx>> exec;
     std::vector<cudaStream_t> streams;
+    // each slot allocates from a memory pool of its own, so slots do not
+    // contend for one pool's lock
+    std::vector<cudaMemPool_t> pools;
     std::vector<std::vector<void *>> bufs;       // column buffers, chunk rows each
     std::vector<std::vector<int>> buf_width;
     std::vector<unsigned long long *> hash;
@@ -103,16 +106,24 @@ struct ServerState {
 
 namespace {
 
-// bytes the context's memory pool has handed out and not taken back
+// bytes the context's memory pool and the slots' pools have handed out and
+// not taken back
 uint64_t pool_bytes(ServerState &S) {
-    cudaMemPool_t pool = S.ctx->s.c.pool;
-    if (!pool) return S.used;
-    size_t v = 0;
-    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) {
-        cudaGetLastError();
-        return S.used;
-    }
-    return (uint64_t)v;
+    uint64_t total = 0;
+    bool any = false;
+    auto add = [&](cudaMemPool_t pool) {
+        if (!pool) return;
+        size_t v = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) == cudaSuccess) {
+            total += (uint64_t)v;
+            any = true;
+        } else {
+            cudaGetLastError();
+        }
+    };
+    add(S.ctx->s.c.pool);
+    for (cudaMemPool_t p : S.pools) add(p);
+    return any ? total : S.used;
 }
 
 void run_one(ServerState &S, int slot, Pending &p) {
@@ -268,6 +279,21 @@ gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, ui
         std::unique_ptr<Ctx> x(new Ctx());
         x->device = ctx->s.c.device;
         x->pool = ctx->s.c.pool;
+        {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = ctx->s.c.device;
+            cudaMemPool_t pool = nullptr;
+            if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+                uint64_t keep = ~0ull;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                x->pool = pool;
+            } else {
+                cudaGetLastError();   // the context's pool then
+            }
+            S.pools.push_back(pool);
+        }
         x->num_sms = ctx->s.c.num_sms;
         x->emit_rpt = ctx->s.c.emit_rpt;
         x->stream = s;
@@ -375,6 +401,7 @@ void gj_server_destroy(gj_server *sv) {
             if (S.exec[i]->pinned) cudaFreeHost(S.exec[i]->pinned);
         }
         if (S.streams[i]) cudaStreamDestroy(S.streams[i]);
+        if (i < (int)S.pools.size() && S.pools[i]) cudaMemPoolDestroy(S.pools[i]);
     }
     if (prev >= 0) cudaSetDevice(prev);
     delete sv;

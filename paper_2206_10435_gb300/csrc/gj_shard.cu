@@ -132,7 +132,7 @@ cudaError_t acc_alloc(Ctx &c, Acc &a, int64_t len, void **mem) {
 // separator must be one attribute.
 bool shard_spec(QueryState &q, int rel, ShardSpec &s) {
     s = ShardSpec{};
-    if (q.tri || rel < 0 || rel >= q.k) return false;
+    if (q.tri || q.cyc || rel < 0 || rel >= q.k) return false;
     QRel &t = q.r[rel];
     if (t.parent >= 0 && t.sep_cols.size() != 1) return false;
     s.G = t.F->G;
@@ -168,7 +168,7 @@ extern "C" {
 gj_status gj_shard_domain(gj_query *q, int32_t rel, int32_t *lo, int32_t *hi) {
     if (!q || !lo || !hi) return GJ_ERR_INVALID;
     QueryState &s = q->s;
-    if (s.tri || rel < 0 || rel >= s.k || s.r[rel].parent < 0) return GJ_ERR_INVALID;
+    if (s.tri || s.cyc || rel < 0 || rel >= s.k || s.r[rel].parent < 0) return GJ_ERR_INVALID;
     const QRel &t = s.r[rel];
     if (t.sep_cols.size() != 1 || t.sep_cols_parent.size() != 1) return GJ_ERR_INVALID;
     const QRel &p = s.r[t.parent];

@@ -74,6 +74,9 @@ struct QRel {
     std::vector<int> sep_cols;         // separator columns in this relation
     std::vector<int> sep_cols_parent;  // matching columns in the parent
     std::vector<int> new_cols;         // columns whose attribute the parent lacks
+    // cyclic queries: for each shared column (sep_cols), the relation that
+    // first holds its attribute and that relation's column
+    std::vector<int> cyc_src_rel, cyc_src_col;
     // segments over the separator (non-root); their number S lives in
     // device memory (*S_dev), arrays are sized for G >= S
     uint32_t *S_dev = nullptr;
@@ -120,6 +123,11 @@ struct QueryState {
     uint64_t nblocks = 0;
     uint64_t *blk_A = nullptr;
     uint32_t *blk_grp[3] = {nullptr, nullptr, nullptr};
+    // a cyclic query answered over one maxclique (gj_cyclic.cu): its blocks'
+    // groups, one array per relation (the first rows in blk_A, their number
+    // in nblocks)
+    bool cyc = false;
+    std::vector<uint32_t *> cyc_grp;
     // relations (with their factors) owned by a summary loaded from a file
     std::vector<std::unique_ptr<Relation>> loaded;
 };

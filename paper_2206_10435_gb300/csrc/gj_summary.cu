@@ -499,9 +499,12 @@ bool dense_link(const QRel &t, const QRel &ch, int64_t *range) {
 
 void tri_free(Ctx &c, QueryState &q);
 gj_status tri_summarize(QueryState &q, uint64_t *total_out);
+void cyc_free(Ctx &c, QueryState &q);
+gj_status cyc_summarize(QueryState &q, uint64_t *total_out);
 
 void query_free_summary(Ctx &c, QueryState &q) {
-    tri_free(c, q);
+    if (q.cyc) cyc_free(c, q);
+    else tri_free(c, q);
     for (auto &t : q.r) {
         dfree(c, t.S_dev);
         dfree(c, t.L_dev);
@@ -524,6 +527,7 @@ void query_free_summary(Ctx &c, QueryState &q) {
 
 gj_status summarize(QueryState &q, uint64_t *total_out) {
     if (q.tri) return tri_summarize(q, total_out);
+    if (q.cyc) return cyc_summarize(q, total_out);
     Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;

@@ -1,0 +1,108 @@
+"""General cyclic queries on the GPU (one-maxclique junction tree, built
+at group level relation by relation) against the oracle's plain
+definition: |Q|, every row (row ids and columns) in canonical order over V
+by first appearance, windows across emit tiles, the empty result, 2^64
+overflow, and the calls with no meaning for a cyclic summary.  Integer
+work: exact equality."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2206_10435_gb300 import datagen as G
+from tests.gpu_util import Run
+from tests.test_oracle import tiny_cyclic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10435_gb300 import gj
+    c = gj.Context(0)
+    yield c
+    c.close()
+
+
+def cyclic_parity(ctx, q, windows=()):
+    run = Run(ctx, q)
+    total = run.summarize()
+    assert total == O.count(q).total
+    if total:
+        j = O.join(q)
+        ref = O.columns(q, j.rowids)
+        cols, rids = run.rows()
+        assert np.array_equal(rids, j.rowids)
+        for a, b in zip(cols, ref):
+            assert np.array_equal(a, b)
+        for r0, n in windows:
+            if r0 >= total:
+                continue
+            cw, rw = run.rows(r0, n)
+            m = min(n, total - r0)
+            assert np.array_equal(rw, j.rowids[r0:r0 + m])
+            for a, b in zip(cw, ref):
+                assert np.array_equal(a, b[r0:r0 + m])
+    run.close()
+    return total
+
+
+TINY = tiny_cyclic()
+
+
+@pytest.mark.parametrize("i", range(len(TINY)))
+def test_tiny_cyclic_queries(ctx, i):
+    cyclic_parity(ctx, TINY[i])
+
+
+# (rows of the first relation, key domain): results of 10^4 .. 2.1 x 10^5 rows
+SIZES = {"square": (300, 24), "pentagon": (120, 12), "bowtie": (50, 8), "diamond": (110, 10),
+         "k4": (60, 8), "wide": (300, 6), "pendant": (70, 10)}
+
+
+@pytest.mark.parametrize("shape", list(G.CYCLIC_SHAPES))
+def test_every_shape_across_emit_tiles(ctx, shape):
+    k = len(G.CYCLIC_SHAPES[shape])
+    base, dom = SIZES[shape]
+    rows = [base + 13 * i for i in range(k)]
+    total = cyclic_parity(ctx, G.cyclic_query(8100 + k, shape, rows, domain=dom, s=0.6),
+                          windows=[(0, 1), (3, 1500), (1023, 4097), (9000, 777)])
+    assert total > 4096
+
+
+def test_empty_result(ctx):
+    # S's B values never meet R's
+    q = G.cyclic_query(3, "square", 50, domain=6)
+    q.relations[1].keys[0] = (q.relations[1].keys[0] + 100).astype(np.int32)
+    assert cyclic_parity(ctx, q) == 0
+
+
+def test_overflow_reported(ctx):
+    from paper_2206_10435_gb300 import gj
+    # a 4-cycle of identical keys: 2^16 rows per relation gives 2^64 rows
+    z = lambda n: np.zeros(n, np.int32)
+    rels = [G.Relation(f"R{i}", list(at), [z(1 << 16), z(1 << 16)])
+            for i, at in enumerate(G.CYCLIC_SHAPES["square"])]
+    run = Run(ctx, G.Query("sq_over", rels))
+    with pytest.raises(gj.GJError) as e:
+        run.summarize()
+    assert e.value.status == gj.GJ_ERR_OVERFLOW
+    run.close()
+    # one row fewer in one relation: 2^64 - 2^48, exact
+    rels[0] = G.Relation("R0", [0, 1], [z((1 << 16) - 1), z((1 << 16) - 1)])
+    run = Run(ctx, G.Query("sq_exact", rels))
+    assert run.summarize() == ((1 << 16) - 1) << 48
+    run.close()
+
+
+def test_tree_only_calls_rejected(ctx):
+    from paper_2206_10435_gb300 import gj
+    run = Run(ctx, G.cyclic_query(9, "square", 30, domain=4))
+    assert run.summarize() > 0
+    for call in (lambda: run.q.level(0, 0, 10), lambda: run.q.summary_groups(0)):
+        with pytest.raises(gj.GJError) as e:
+            call()
+        assert e.value.status == gj.GJ_ERR_INVALID
+    run.close()
