@@ -263,6 +263,9 @@ __device__ __forceinline__ bool sep_head(const KeyCols &sep, int64_t g) {
     return false;
 }
 
+// NCH >= 0: exactly NCH children; NCH < 0: s.nch.  SEP1: the separator is
+// one column (heads found from a staged copy of it), else any number.
+template <int NCH, bool SEP1>
 __global__ void __launch_bounds__(ST)
 k_up_scan(UpSpec s) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -281,18 +284,62 @@ k_up_scan(UpSpec s) {
     const int64_t base = (int64_t)tile * UP_TILE;
     if (base >= s.G) return;
     const int tile_n = (int)min((int64_t)UP_TILE, s.G - base);
-    // elements, coalesced: w = cnt (x) children's messages; head; (live = w > 0)
-    for (int e = tid; e < UP_TILE; e += ST) {
-        const int64_t g = base + e;
+    // elements, coalesced (element e = tid + i * ST): every independent load
+    // of the tile is issued before the first use -- group starts, separator
+    // keys, the children's links -- then the messages behind the links
+    uint32_t *s_gs = s_xh;              // group starts [0, tile_n]; s_xh is free until the scan
+    int32_t *s_key = (int32_t *)s_xl;   // separator key of element e at e + 1; [0] the one before
+    const int nch = NCH >= 0 ? NCH : s.nch;
+    uint32_t gs[UP_ITEMS];
+    int32_t key[UP_ITEMS];
+    uint64_t prod[UP_ITEMS];
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; i++) {
+        const int e = tid + i * ST;
+        const bool in = e < tile_n;
+        gs[i] = in ? __ldg(s.gstart + base + e) : 0u;
+        if (SEP1) key[i] = in && s.seg ? __ldg(s.sep.col[0] + base + e) : 0;
+        prod[i] = 1;
+    }
+    if (tid == 0) {
+        s_gs[tile_n] = __ldg(s.gstart + base + tile_n);
+        if (SEP1) s_key[0] = base > 0 && s.seg ? __ldg(s.sep.col[0] + base - 1) : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < (NCH >= 0 ? NCH : MAX_REL); c++) {
+        if (NCH < 0 && c >= nch) break;
+        const uint32_t *lk = s.link[c];
+        const unsigned long long *mg = (const unsigned long long *)s.msg[c];
+        uint32_t l[UP_ITEMS];
+#pragma unroll
+        for (int i = 0; i < UP_ITEMS; i++) {
+            const int e = tid + i * ST;
+            l[i] = e < tile_n ? __ldg(lk + base + e) : NONE;
+        }
+#pragma unroll
+        for (int i = 0; i < UP_ITEMS; i++)
+            prod[i] = sat_mul(prod[i], l[i] == NONE ? 0ull : __ldg(mg + l[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; i++) {
+        const int e = tid + i * ST;
+        if (e < tile_n) s_gs[e] = gs[i];   // [tile_n] is thread 0's
+        if (SEP1) s_key[e + 1] = key[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < UP_ITEMS; i++) {
+        const int e = tid + i * ST;
         uint64_t w = 0;
         uint8_t h = 0;
         if (e < tile_n) {
-            w = (uint64_t)(__ldg(s.gstart + g + 1) - __ldg(s.gstart + g));
-            for (int i = 0; i < s.nch; i++) {
-                const uint32_t l = __ldg(s.link[i] + g);
-                w = sat_mul(w, l == NONE ? 0ull : __ldg((const unsigned long long *)s.msg[i] + l));
+            // w = cnt (x) prod of the children's messages (the semiring
+            // product is associative and commutative)
+            w = sat_mul((uint64_t)(s_gs[e + 1] - s_gs[e]), prod[i]);
+            if (s.seg) {
+                if (SEP1) h = (base + e == 0) || s_key[e + 1] != s_key[e];
+                else h = sep_head(s.sep, base + e);
             }
-            h = s.seg ? sep_head(s.sep, g) : 0;
         }
         s_w[p64(e)] = w;
         s_h[e] = h;
@@ -382,6 +429,32 @@ k_up_scan(UpSpec s) {
     }
 }
 
+template <int NCH, bool SEP1>
+cudaError_t launch_up_scan_k(Ctx &c, const UpSpec &u) {
+    cudaError_t e = cudaFuncSetAttribute(k_up_scan<NCH, SEP1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)UP_SMEM);
+    if (e != cudaSuccess) return e;
+    k_up_scan<NCH, SEP1><<<(unsigned)ceil_div(u.G, UP_TILE), ST, UP_SMEM, c.stream>>>(u);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+template <bool SEP1>
+cudaError_t launch_up_scan_t(Ctx &c, const UpSpec &u) {
+    switch (u.nch) {
+        case 0: return launch_up_scan_k<0, SEP1>(c, u);
+        case 1: return launch_up_scan_k<1, SEP1>(c, u);
+        case 2: return launch_up_scan_k<2, SEP1>(c, u);
+        case 3: return launch_up_scan_k<3, SEP1>(c, u);
+        case 4: return launch_up_scan_k<4, SEP1>(c, u);
+        default: return launch_up_scan_k<-1, SEP1>(c, u);
+    }
+}
+
+cudaError_t launch_up_scan(Ctx &c, const UpSpec &u) {
+    return (!u.seg || u.sep.ncol == 1) ? launch_up_scan_t<true>(c, u) : launch_up_scan_t<false>(c, u);
+}
+
 // ------------------------------------------------------------ downward
 // A child's down message, accumulated exactly: lo = sum of the
 // contributions' low 32-bit halves, hi = sum of their high halves (fewer
@@ -416,52 +489,211 @@ struct DownSpec {
     const uint32_t *link[MAX_REL];
     const uint64_t *msg[MAX_REL];
     DownAcc acc[MAX_REL];
+    uint8_t agg[MAX_REL];              // combine child c's contributions per block
 };
 
-// NCH > 0: exactly NCH children (register arrays); NCH < 0: s.nch children
+// Contributions to a child's down message are combined per block before
+// they reach global memory when the parent's links to that child are not in
+// key order: parent groups of skewed keys send many contributions to the
+// same child segment (on a Zipf(1.1) chain, 3.6% of a relation's groups
+// link to its most common key), and atomics on one address serialise.
+// Each round a block accumulates contributions in a small open-addressing
+// table in shared memory, segment -> 16-bit pieces of the sum (32-bit
+// counters: a round adds at most ST * DN_ITEMS pieces below 2^16, so none
+// wraps) and a SAT flag; once the table is full, contributions of new
+// segments go to the global accumulators directly.  A key that recurs in a
+// round (the hot ones) claims a slot early and is added once per round
+// and block.  At the end of the round every claimed slot is added to the
+// global split-word accumulators.  Integer sums: exact in any order.
+// Links in key order (the child joins the parent's leading columns) go
+// straight to the global accumulators.  A block also stops using the table
+// for a child while fewer than one in AGG_MIN_HIT of a round's
+// contributions find their key already there (keys without repeats: the
+// table would only add work), and tries it again every AGG_RETRY rounds.
+constexpr int AGG_BITS = 8;
+constexpr int AGG = 1 << AGG_BITS;
+constexpr int AGG_PROBES = 2;
+constexpr uint32_t AGG_MIN_HIT = 16;
+constexpr int AGG_RETRY = 8;
+
+struct AggTable {
+    uint32_t key[AGG];
+    uint32_t piece[4][AGG];   // the sum's bits [16 p, 16 p + 16), p = 0..3, summed
+    uint32_t sat[AGG];
+};
+
+__device__ __forceinline__ void acc_add_global(const DownAcc &a, uint32_t l, uint64_t x) {
+    if (x == SAT) {
+        atomicOr(a.sat + l, 1u);
+        return;
+    }
+    // results unused: compiled to fire-and-forget reductions
+    atomicAdd(a.lo + l, (unsigned long long)(x & 0xffffffffull));
+    if (x >> 32) atomicAdd(a.hi + l, (unsigned long long)(x >> 32));
+}
+
+// Returns 1 when l already had a slot (a repeated key).
+__device__ __forceinline__ uint32_t agg_add(AggTable &t, const DownAcc &a, uint32_t l, uint64_t x) {
+    uint32_t slot = (l * 0x9E3779B1u) >> (32 - AGG_BITS);
+#pragma unroll
+    for (int p = 0; p < AGG_PROBES; p++) {
+        uint32_t k = *(volatile uint32_t *)(t.key + slot);
+        if (k == NONE) k = atomicCAS(t.key + slot, NONE, l);   // the old value: NONE = claimed now
+        if (k == NONE || k == l) {
+            if (x == SAT) {
+                atomicOr(t.sat + slot, 1u);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t v = (uint32_t)(x >> (16 * q)) & 0xffffu;
+                    if (v) atomicAdd(&t.piece[q][slot], v);
+                }
+            }
+            return k == l ? 1u : 0u;
+        }
+        slot = (slot + 1) & (AGG - 1);
+    }
+    acc_add_global(a, l, x);
+    return 0;
+}
+
+// NCH >= 0: exactly NCH children, DN_ITEMS groups per thread and round with
+// every independent load issued before the first use, contributions
+// combined per block (dynamic shared memory AGG_SMEM when NCH > 0);
+// NCH < 0: s.nch children, one group per thread and round, contributions
+// straight to the global accumulators
+constexpr int DN_ITEMS = 4;
+
 template <int NCH>
 __global__ void __launch_bounds__(ST)
 k_down(DownSpec s) {
     constexpr int CAP = NCH >= 0 ? (NCH > 0 ? NCH : 1) : MAX_REL;
+    constexpr int IT = NCH >= 0 ? DN_ITEMS : 1;
     const int nch = NCH >= 0 ? NCH : s.nch;
-    GRID_LOOP(g, s.G) {
-        uint64_t base = (uint64_t)(__ldg(s.gstart + g + 1) - __ldg(s.gstart + g));
-        const uint64_t w = __ldg((const unsigned long long *)s.w + g);
-        if (s.has_down) {
-            const uint32_t sid = __ldg(s.seg_id + g);
-            const uint64_t d = down_value(s.self, sid);
-            if (__ldg(s.seg_first + sid) == (uint32_t)g) s.down_out[sid] = d;
-            base = sat_mul(base, d);
-            s.mult[g] = sat_mul(w, d);
-        } else {
-            s.mult[g] = w;
+    __shared__ AggTable tab;
+    __shared__ uint32_t s_use[CAP], s_hits[CAP];
+    if (NCH > 0 && threadIdx.x < CAP) s_use[threadIdx.x] = 1;   // seen after the first barrier
+    const int64_t step = (int64_t)gridDim.x * ST * IT;
+    // b0 is the same for every thread of the block: the rounds (and the
+    // barriers in them) are uniform
+    int round = 0;
+    for (int64_t b0 = (int64_t)blockIdx.x * ST * IT; b0 < s.G; b0 += step, round++) {
+        int64_t g[IT];
+        bool in[IT];
+        uint32_t g0[IT], g1[IT], sid[IT];
+        uint64_t w[IT];
+#pragma unroll
+        for (int i = 0; i < IT; i++) {
+            g[i] = b0 + threadIdx.x + (int64_t)i * ST;
+            in[i] = g[i] < s.G;
+            g0[i] = in[i] ? __ldg(s.gstart + g[i]) : 0u;
+            g1[i] = in[i] ? __ldg(s.gstart + g[i] + 1) : 0u;
+            w[i] = in[i] ? __ldg((const unsigned long long *)s.w + g[i]) : 0ull;
+            sid[i] = in[i] && s.has_down ? __ldg(s.seg_id + g[i]) : 0u;
         }
+        uint32_t l[CAP][IT];
         if constexpr (NCH != 0) {
-            if (base == 0) continue;
-            uint32_t l[CAP];
-            uint64_t m[CAP];
 #pragma unroll
-            for (int i = 0; i < CAP; i++) {
-                if (i >= nch) break;
-                l[i] = __ldg(s.link[i] + g);
-                m[i] = l[i] == NONE ? 0ull : __ldg((const unsigned long long *)s.msg[i] + l[i]);
+            for (int c = 0; c < CAP; c++) {
+                if (c >= nch) break;
+#pragma unroll
+                for (int i = 0; i < IT; i++) l[c][i] = in[i] ? __ldg(s.link[c] + g[i]) : NONE;
             }
+        }
+        uint64_t d[IT];
+        uint32_t first[IT];
 #pragma unroll
-            for (int i = 0; i < CAP; i++) {
-                if (i >= nch) break;
-                if (l[i] == NONE) continue;
-                uint64_t x = base;
+        for (int i = 0; i < IT; i++) {
+            d[i] = 1;
+            first[i] = NONE;
+            if (in[i] && s.has_down) {
+                d[i] = down_value(s.self, sid[i]);
+                first[i] = __ldg(s.seg_first + sid[i]);
+            }
+        }
+        uint64_t m[CAP][IT];
+        if constexpr (NCH != 0) {
 #pragma unroll
-                for (int j = 0; j < CAP; j++)
-                    if (j < nch && j != i) x = sat_mul(x, m[j]);
-                if (x == 0) continue;
-                if (x == SAT) {
-                    atomicOr(s.acc[i].sat + l[i], 1u);
+            for (int c = 0; c < CAP; c++) {
+                if (c >= nch) break;
+#pragma unroll
+                for (int i = 0; i < IT; i++)
+                    m[c][i] = l[c][i] == NONE ? 0ull : __ldg((const unsigned long long *)s.msg[c] + l[c][i]);
+            }
+        }
+        // mult, the relation's own down message; base = cnt (x) down
+        uint64_t base[IT];
+#pragma unroll
+        for (int i = 0; i < IT; i++) {
+            base[i] = 0;
+            if (!in[i]) continue;
+            base[i] = (uint64_t)(g1[i] - g0[i]);
+            if (s.has_down) {
+                if (first[i] == (uint32_t)g[i]) s.down_out[sid[i]] = d[i];
+                base[i] = sat_mul(base[i], d[i]);
+                s.mult[g[i]] = sat_mul(w[i], d[i]);
+            } else {
+                s.mult[g[i]] = w[i];
+            }
+        }
+        if constexpr (NCH > 0) {
+            // child c's contributions: base (x) the other children's messages
+#pragma unroll
+            for (int c = 0; c < NCH; c++) {
+                uint64_t x[IT];
+#pragma unroll
+                for (int i = 0; i < IT; i++) {
+                    x[i] = l[c][i] == NONE ? 0ull : base[i];
+#pragma unroll
+                    for (int j = 0; j < NCH; j++)
+                        if (j != c) x[i] = sat_mul(x[i], m[j][i]);
+                }
+                bool use = s.agg[c] != 0;   // the same for the whole grid
+                if (use) {
+                    __syncthreads();   // the table's previous use is over; s_use is settled
+                    use = s_use[c] || round % AGG_RETRY == 0;   // the same for the block
+                }
+                if (!use) {
+#pragma unroll
+                    for (int i = 0; i < IT; i++)
+                        if (x[i]) acc_add_global(s.acc[c], l[c][i], x[i]);
                     continue;
                 }
-                // results unused: compiled to fire-and-forget reductions
-                atomicAdd(s.acc[i].lo + l[i], (unsigned long long)(x & 0xffffffffull));
-                if (x >> 32) atomicAdd(s.acc[i].hi + l[i], (unsigned long long)(x >> 32));
+                for (int j = threadIdx.x; j < AGG; j += ST) {
+                    tab.key[j] = NONE;
+                    tab.piece[0][j] = tab.piece[1][j] = tab.piece[2][j] = tab.piece[3][j] = 0;
+                    tab.sat[j] = 0;
+                }
+                if (threadIdx.x == 0) s_hits[c] = 0;
+                __syncthreads();
+                uint32_t hits = 0;
+#pragma unroll
+                for (int i = 0; i < IT; i++)
+                    if (x[i]) hits += agg_add(tab, s.acc[c], l[c][i], x[i]);
+                hits = __reduce_add_sync(0xffffffffu, hits);
+                if ((threadIdx.x & 31) == 0 && hits) atomicAdd(&s_hits[c], hits);
+                __syncthreads();
+                if (threadIdx.x == 0) s_use[c] = s_hits[c] * AGG_MIN_HIT >= (uint32_t)(ST * IT);
+                for (int j = threadIdx.x; j < AGG; j += ST) {
+                    const uint32_t k = tab.key[j];
+                    if (k == NONE) continue;
+                    if (tab.sat[j]) atomicOr(s.acc[c].sat + k, 1u);
+                    const unsigned long long lo = (unsigned long long)tab.piece[0][j] +
+                                                  ((unsigned long long)tab.piece[1][j] << 16);
+                    const unsigned long long hi = (unsigned long long)tab.piece[2][j] +
+                                                  ((unsigned long long)tab.piece[3][j] << 16);
+                    if (lo) atomicAdd(s.acc[c].lo + k, lo);
+                    if (hi) atomicAdd(s.acc[c].hi + k, hi);
+                }
+            }
+        } else if constexpr (NCH < 0) {
+            if (base[0] == 0) continue;
+            for (int c = 0; c < nch; c++) {
+                if (l[c][0] == NONE) continue;
+                uint64_t x = base[0];
+                for (int j = 0; j < nch; j++)
+                    if (j != c) x = sat_mul(x, m[j][0]);
+                if (x != 0) acc_add_global(s.acc[c], l[c][0], x);
             }
         }
     }
@@ -578,7 +810,6 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
         if (dense_end > zero_end) TRY(cudaMemsetAsync(scratch + zero_end, 0xFF, dense_end - zero_end, c.stream));
         if (bytes > dense_end) TRY(cudaMemsetAsync(scratch + dense_end, 0, bytes - dense_end, c.stream));
         uint64_t *total_dev = (uint64_t *)scratch;
-        TRY(cudaFuncSetAttribute(k_up_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UP_SMEM));
         // upward, leaves to root (reverse preorder): links to the children
         // (whose segments exist by now), then the relation's scan
         for (int pi = q.k - 1; pi >= 0; pi--) {
@@ -657,8 +888,7 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
             u.status = (ulonglong2 *)(scratch + st_off[ti] + 16);
             u.counter = (uint32_t *)(scratch + st_off[ti]);
             u.err = c.err;
-            k_up_scan<<<(unsigned)ceil_div(G, UP_TILE), ST, UP_SMEM, c.stream>>>(u); c.launches++;
-            TRY(cudaGetLastError());
+            TRY(launch_up_scan(c, u));
         }
         // downward, root to leaves (preorder): mult, each child's down
         // message, and the relation's own down message finished
@@ -686,6 +916,11 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
                 d.link[ci] = t.link[ci];
                 d.msg[ci] = q.r[t.children[ci]].msg;
                 d.acc[ci] = acc_of(t.children[ci]);
+                // links in key order when the child joins the parent's
+                // leading factor columns: no combining needed
+                const std::vector<int> &sp = q.r[t.children[ci]].sep_cols_parent;
+                const std::vector<int> &ord = t.F->order;
+                d.agg[ci] = !(sp.size() <= ord.size() && std::equal(sp.begin(), sp.end(), ord.begin()));
             }
             launch_down(c, grid_for(c, G), d);
             TRY(cudaGetLastError());

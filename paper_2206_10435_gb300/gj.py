@@ -12,6 +12,7 @@ The entry points keep the C names (``gj_create``, ``gj_load_relation``,
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 import re
 
@@ -197,9 +198,17 @@ class Context:
         _check(L.gj_create(ctypes.byref(h), device, _P(stream.cuda_stream)), "gj_create")
         self.h = h
         self._keep = {}
+        self._owned = weakref.WeakSet()   # queries, batches, servers on this context
+
+    def _own(self, obj):
+        self._owned.add(obj)
 
     def close(self):
+        """Destroys the context; queries, batches and servers still open on
+        it are closed first (their handles point into it)."""
         if self.h:
+            for obj in list(self._owned):
+                obj.close()
             lib().gj_destroy(self.h)
             self.h = None
 
@@ -296,6 +305,7 @@ class Query:
             _check(lib().gj_query_create(ctx.h, ids, len(rel_ids), ctypes.byref(h)),
                    "gj_query_create")
         self.h = h
+        ctx._own(self)
         s = QuerySizes()
         _check(lib().gj_query_sizes(self.h, ctypes.byref(s)), "gj_query_sizes")
         self.n_rel = s.n_rel
@@ -466,6 +476,7 @@ class Batch:
         _check(lib().gj_batch_create(ctx.h, _i32(flat), _i32(off), len(queries_rel_ids),
                                      ctypes.byref(h)), "gj_batch_create")
         self.h = h
+        ctx._own(self)
         self.n_queries = len(queries_rel_ids)
         n = ctypes.c_int64()
         r, l, kb = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -509,6 +520,7 @@ class NativeServer:
         _check(lib().gj_server_create(ctx.h, n_slots, hbm_budget, chunk_rows, max_rows, ctypes.byref(h)),
                "gj_server_create")
         self.h = h
+        ctx._own(self)
 
     def run(self, queries_rel_ids, arrival_offsets):
         """queries_rel_ids[i] arrives arrival_offsets[i] s after the start.
