@@ -341,38 +341,49 @@ k_group_scan(GroupScanSpec s, int64_t n) {
         if (MODE == 2) s_hi[0] = base > 0 ? s.hi[base - 1] : 0ull;
     }
     __syncthreads();
-    // heads among the thread's 16 consecutive rows
-    uint32_t hmask = 0;
+    // heads, row e = i * GS_THREADS + tid: one ballot per warp and i; the
+    // tile's head counts per (i, warp) in row order, then their exclusive
+    // prefix (warp 0, four entries a lane)
+    __shared__ uint32_t s_cnt[GS_ITEMS * (GS_THREADS / 32)];
+    __shared__ uint32_t s_hb[GS_ITEMS * (GS_THREADS / 32)];   // the ballots
+    static_assert(GS_ITEMS * (GS_THREADS / 32) == 128, "four prefix entries per lane of warp 0");
 #pragma unroll
     for (int i = 0; i < GS_ITEMS; i++) {
-        const int e = tid * GS_ITEMS + i;
+        const int e = i * GS_THREADS + tid;
+        bool h = false;
         if (e < tile_n) {
             const uint64_t a = s_lo[gs_slot(e + 1)], b = s_lo[gs_slot(e)];
-            bool h;
             if (MODE == 0) h = (a >> s.row_bits) != (b >> s.row_bits);
             else if (MODE == 1) h = a != b;
             else h = a != b || s_hi[gs_slot(e + 1)] != s_hi[gs_slot(e)];
-            if (h || base + e == 0) hmask |= 1u << i;
+            h = h || base + e == 0;
+        }
+        const uint32_t hb = __ballot_sync(0xffffffffu, h);
+        if (lane == 0) {
+            s_cnt[i * (GS_THREADS / 32) + warp] = __popc(hb);
+            s_hb[i * (GS_THREADS / 32) + warp] = hb;
         }
     }
-    // tile-wide exclusive count of heads, then the carry-in by lookback
-    const uint32_t cnt = __popc(hmask);
-    uint32_t x = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = x;
     __syncthreads();
-    uint32_t before = 0, agg = 0;
+    uint32_t agg = 0;
+    if (warp == 0) {
+        uint32_t v[4], sum = 0;
 #pragma unroll
-    for (int w = 0; w < GS_THREADS / 32; w++) {
-        const uint32_t v = s_wsum[w];
-        if (w < warp) before += v;
-        agg += v;
+        for (int j = 0; j < 4; j++) { v[j] = s_cnt[lane * 4 + j]; sum += v[j]; }
+        uint32_t x = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        agg = __shfl_sync(0xffffffffu, x, 31);
+        uint32_t run = x - sum;
+#pragma unroll
+        for (int j = 0; j < 4; j++) { s_cnt[lane * 4 + j] = run; run += v[j]; }
+        if (lane == 0) s_wsum[0] = agg;
     }
-    const uint32_t excl = before + x - cnt;
+    __syncthreads();
+    agg = s_wsum[0];
     // the tile's aggregate goes out first; the row order and the payloads do
     // not depend on the group numbering, so they are gathered while the
     // lookback waits on the predecessors
@@ -430,13 +441,18 @@ k_group_scan(GroupScanSpec s, int64_t n) {
         }
     }
     __syncthreads();
-    // group starts and keys
-    uint32_t g = s_carry + excl;
-    while (hmask) {
-        const int i = __ffs(hmask) - 1;
-        hmask &= hmask - 1;
-        const int e = tid * GS_ITEMS + i;
+    // group starts and keys, row e = i * GS_THREADS + tid: the heads of one
+    // (i, warp) take consecutive group numbers, so the stores of a warp are
+    // contiguous where heads are dense
+    const uint32_t carry = s_carry;
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll 1
+    for (int i = 0; i < GS_ITEMS; i++) {
+        const uint32_t hb = s_hb[i * (GS_THREADS / 32) + warp];
+        if (!((hb >> lane) & 1u)) continue;
+        const int e = i * GS_THREADS + tid;
         const int64_t idx = base + e;
+        const uint32_t g = carry + s_cnt[i * (GS_THREADS / 32) + warp] + __popc(hb & lt);
         s.gstart[g] = (uint32_t)idx;
         const uint64_t klo = s_lo[gs_slot(e + 1)], khi = MODE == 2 ? s_hi[gs_slot(e + 1)] : 0ull;
         for (int c = 0; c < s.u.ncol; c++) {
@@ -450,7 +466,6 @@ k_group_scan(GroupScanSpec s, int64_t n) {
             for (int c = 0; c < s.u.nother; c++)
                 s.gkey[(int64_t)s.u.other_col[c] * s.gkey_stride + g] = s.u.other[c][r];
         }
-        g++;
     }
 }
 
@@ -469,7 +484,7 @@ struct RunSortSpec {
     int row_bits;
     const uint32_t *run_start;    // [R + 1]
     const uint32_t *R_dev;        // number of runs
-    PackSrc rest;                 // the remaining columns, packed from bit 0
+    const uint64_t *rest;         // [n] the remaining columns of each row, packed from bit 0
     uint64_t *hi;                 // out: the leading columns' word
     uint64_t *lo;                 // out: the remaining columns' word
     uint32_t *perm;               // out: row ids
@@ -529,7 +544,7 @@ __device__ __forceinline__ void sort_run(const RunSortSpec &s, uint32_t p0, uint
         row[k] = e < m ? (uint32_t)(__ldg((const unsigned long long *)s.a + p0 + e) & rmask) : 0xffffffffu;
     }
 #pragma unroll
-    for (int k = 0; k < E; k++) key[k] = row[k] != 0xffffffffu ? pack_word(s.rest, row[k]) : ~0ull;
+    for (int k = 0; k < E; k++) key[k] = row[k] != 0xffffffffu ? __ldg((const unsigned long long *)s.rest + row[k]) : ~0ull;
     warp_bitonic<E>(key, row, lane);
     const uint64_t lead = __ldg((const unsigned long long *)s.a + p0) >> s.row_bits;
 #pragma unroll
@@ -569,6 +584,13 @@ __global__ void __launch_bounds__(256) k_sort_runs(RunSortSpec s) {
             }
         }
     }
+}
+
+// the remaining columns of every row packed into one word, in row order
+// (sequential reads), so that the run sort gathers one word per row
+__global__ void k_pack_rest(PackSrc ps, int64_t n, uint64_t *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * FT + threadIdx.x; i < n; i += (int64_t)gridDim.x * FT)
+        out[i] = pack_word(ps, i);
 }
 
 // run heads of the sorted words: the leading columns differ from the
@@ -814,7 +836,11 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             rs.row_bits = row_bits;
             rs.run_start = run_start;
             rs.R_dev = R_dev;
-            rs.rest = pack_src(R, rest, bits, 0);
+            uint64_t *restw = nullptr;
+            GJ_CUDA_TRY(tmp.alloc(&restw, n));
+            k_pack_rest<<<grid_for(c, n), FT, 0, c.stream>>>(pack_src(R, rest, bits, 0), n, restw); c.launches++;
+            GJ_CUDA_TRY(cudaGetLastError());
+            rs.rest = restw;
             rs.hi = hiw;
             rs.lo = low;
             rs.perm = F.perm;
@@ -825,6 +851,7 @@ cudaError_t fb_sort(Ctx &c, FactorBuild &b) {
             tmp.free(excl);
             tmp.free(run_start);
             tmp.free(R_dev);
+            tmp.free(restw);
             gs.lo = low;
             gs.hi = hiw;
             gs.perm_in = F.perm;
