@@ -66,6 +66,13 @@ struct Ctx {
     bool test_stall = false;
     int64_t fail_alloc_at = 0;
     int64_t allocs = 0;
+    // bump arena (a serving slot's): while arena_on, allocations come from
+    // it as long as it has room, and frees of its memory are no-ops; the
+    // owner rewinds arena_used once nothing enqueued later on this stream
+    // needs what lies past the mark (the stream orders reuse)
+    char *arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
+    bool arena_on = false;
     // device-time profile of the emit kernel (CUDA events on the stream)
     bool prof = false;
     std::vector<cudaEvent_t> ev_free, ev_used;     // emit kernel: start/stop pairs
@@ -87,24 +94,38 @@ inline bool fail_this_alloc(Ctx &c) {
     return c.fail_alloc_at > 0 && c.allocs == c.fail_alloc_at;
 }
 
-template <class T>
-inline cudaError_t dalloc(Ctx &c, T **p, size_t count) {
-    *p = nullptr;
-    if (fail_this_alloc(c)) return cudaErrorMemoryAllocation;
-    if (count == 0) count = 1;
-    if (c.pool) return cudaMallocFromPoolAsync((void **)p, count * sizeof(T), c.pool, c.stream);
-    return cudaMallocAsync((void **)p, count * sizeof(T), c.stream);
+inline bool in_arena(const Ctx &c, const void *p) {
+    return c.arena && (const char *)p >= c.arena && (const char *)p < c.arena + c.arena_size;
 }
+
+// bytes from the arena (256-byte aligned), or NULL
+inline void *arena_take(Ctx &c, size_t bytes) {
+    if (!c.arena_on) return nullptr;
+    const size_t b = (bytes + 255) & ~(size_t)255;
+    if (b > c.arena_size - c.arena_used) return nullptr;
+    void *p = c.arena + c.arena_used;
+    c.arena_used += b;
+    return p;
+}
+
 inline cudaError_t dalloc_bytes(Ctx &c, void **p, size_t bytes) {
     *p = nullptr;
     if (fail_this_alloc(c)) return cudaErrorMemoryAllocation;
     if (bytes == 0) bytes = 1;
+    if ((*p = arena_take(c, bytes)) != nullptr) return cudaSuccess;
     if (c.pool) return cudaMallocFromPoolAsync(p, bytes, c.pool, c.stream);
     return cudaMallocAsync(p, bytes, c.stream);
 }
 template <class T>
+inline cudaError_t dalloc(Ctx &c, T **p, size_t count) {
+    return dalloc_bytes(c, (void **)p, (count == 0 ? 1 : count) * sizeof(T));
+}
+inline void dfree_bytes(Ctx &c, void *p) {
+    if (p && !in_arena(c, p)) cudaFreeAsync(p, c.stream);
+}
+template <class T>
 inline void dfree(Ctx &c, T *&p) {
-    if (p) cudaFreeAsync((void *)p, c.stream);
+    dfree_bytes(c, (void *)p);
     p = nullptr;
 }
 
@@ -117,7 +138,7 @@ class Temps {
     Temps(const Temps &) = delete;
     Temps &operator=(const Temps &) = delete;
     ~Temps() {
-        for (void *p : p_) cudaFreeAsync(p, c_.stream);
+        for (void *p : p_) dfree_bytes(c_, p);
     }
     template <class T>
     cudaError_t alloc(T **p, size_t count) {

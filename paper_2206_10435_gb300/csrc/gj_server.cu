@@ -32,6 +32,11 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
 
 namespace {
 
+// device memory of one slot's requests, taken by bumping a pointer: a
+// request (summary, and each result chunk's temporaries) that needs more
+// continues in the slot's pool
+constexpr size_t SLOT_ARENA = (size_t)512 << 20;
+
 // Order-independent, position-dependent hash of a result chunk: the
 // xor over rows and columns of a 64-bit mix of (column, row, value).
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -130,10 +135,19 @@ void run_one(ServerState &S, int slot, Pending &p) {
     gj_request_result &r = S.results[p.idx];
     gj_query *q = p.q;
     r.slot = slot;
-    q->s.exec = S.exec[slot].get();
+    Ctx &x = *S.exec[slot];
+    q->s.exec = &x;
     gj_status st = GJ_OK;
     uint64_t total = 0;
+    // the request's device memory comes from the slot's arena while it has
+    // room: no allocator calls (which every slot's thread would otherwise
+    // make by the dozen per request) and frees that cost nothing.  The
+    // arena starts empty: the previous request's work was enqueued on this
+    // same stream, before anything that reuses its memory.
+    x.arena_used = 0;
+    x.arena_on = x.arena != nullptr;
     if (st == GJ_OK) st = gj_summarize(q, &total);
+    x.arena_on = false;   // the slot's long-lived buffers below come from the pool
     r.total = total;
     r.t_summary = now_s();
     if (st == GJ_OK && total > 0) {
@@ -155,12 +169,18 @@ void run_one(ServerState &S, int slot, Pending &p) {
         }
         // stream the result (up to the row limit) chunk by chunk; the hash
         // of every chunk accumulates on the device, and each chunk's
-        // desummarisation waits for the previous one to be hashed
+        // desummarisation waits for the previous one to be hashed.  A
+        // chunk's temporaries come from the slot's arena past the summary's
+        // arrays and are rewound after it (later chunks reuse them in
+        // stream order).
         const uint64_t want = S.max_rows ? std::min<uint64_t>(S.max_rows, total) : total;
         if (st == GJ_OK) cudaMemsetAsync(S.hash[slot], 0, 8, c.stream);
+        const size_t mark = c.arena_used;
+        c.arena_on = c.arena != nullptr;
         uint64_t done = 0;
         while (st == GJ_OK && done < want) {
             uint64_t n = 0;
+            c.arena_used = mark;
             st = desummarize(qs, done, std::min<uint64_t>(S.chunk, want - done), bufs.data(), nullptr, &n);
             if (st != GJ_OK || n == 0) break;
             ChunkCols cc{};
@@ -180,6 +200,7 @@ void run_one(ServerState &S, int slot, Pending &p) {
             r.hash = S.hash_host[slot][0];
         }
     }
+    x.arena_on = false;
     r.status = st;
     r.t_last = now_s();
     if (r.t_chunk == 0) r.t_chunk = r.t_last;
@@ -303,6 +324,18 @@ gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, ui
             st = GJ_ERR_CUDA;
         }
         if (x->err) cudaMemset(x->err, 0, 16);
+        // the slot's arena, from its pool (so that admission counts it)
+        if (st == GJ_OK && SLOT_ARENA > 0) {
+            void *a = nullptr;
+            cudaError_t e = x->pool ? cudaMallocFromPoolAsync(&a, SLOT_ARENA, x->pool, s)
+                                    : cudaMallocAsync(&a, SLOT_ARENA, s);
+            if (e == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess) {
+                x->arena = (char *)a;
+                x->arena_size = SLOT_ARENA;
+            } else {
+                cudaGetLastError();   // no arena: the slot allocates from its pool
+            }
+        }
         S.exec.push_back(std::move(x));
     }
     S.bufs.assign(n_slots, {});
@@ -397,6 +430,7 @@ void gj_server_destroy(gj_server *sv) {
         if (S.hash[i]) cudaFree(S.hash[i]);
         if (S.hash_host[i]) cudaFreeHost(S.hash_host[i]);
         if (i < (int)S.exec.size() && S.exec[i]) {
+            if (S.exec[i]->arena) cudaFreeAsync(S.exec[i]->arena, S.streams[i]);
             if (S.exec[i]->err) cudaFree(S.exec[i]->err);
             if (S.exec[i]->pinned) cudaFreeHost(S.exec[i]->pinned);
         }

@@ -39,6 +39,7 @@
 // contributions' 32-bit halves (the true sum is recovered in 128 bits, so
 // saturation is exact).
 #include <algorithm>
+#include <atomic>
 
 #include "gj_lookback.cuh"
 #include "gj_state.cuh"
@@ -431,9 +432,15 @@ k_up_scan(UpSpec s) {
 
 template <int NCH, bool SEP1>
 cudaError_t launch_up_scan_k(Ctx &c, const UpSpec &u) {
-    cudaError_t e = cudaFuncSetAttribute(k_up_scan<NCH, SEP1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)UP_SMEM);
-    if (e != cudaSuccess) return e;
+    // the shared-memory limit is set once per device (devices 0..63)
+    static std::atomic<uint64_t> set_on{0};
+    const uint64_t bit = 1ull << (c.device & 63);
+    if (!(set_on.load(std::memory_order_acquire) & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(k_up_scan<NCH, SEP1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)UP_SMEM);
+        if (e != cudaSuccess) return e;
+        set_on.fetch_or(bit, std::memory_order_release);
+    }
     k_up_scan<NCH, SEP1><<<(unsigned)ceil_div(u.G, UP_TILE), ST, UP_SMEM, c.stream>>>(u);
     c.launches++;
     return cudaGetLastError();
