@@ -114,6 +114,11 @@ struct QueryState {
     bool summarized = false;
     bool overflow = false;
     uint64_t total = 0;
+    // one allocation holding every per-relation array of the summary (NULL
+    // when they were allocated one by one: a loaded summary, or a serving
+    // slot's arena)
+    void *slab = nullptr;
+    size_t slab_bytes = 0;
     // the cyclic 3-way join (gj_cycle.cu): key columns per relation
     // {shared with the previous relation, shared with the next} in the
     // cycle R0 -> R1 -> R2 -> R0, and its blocks (group triples) in result

@@ -744,23 +744,35 @@ gj_status cyc_summarize(QueryState &q, uint64_t *total_out);
 void query_free_summary(Ctx &c, QueryState &q) {
     if (q.cyc) cyc_free(c, q);
     else tri_free(c, q);
+    // arrays inside the slab are forgotten, any other one freed; then the
+    // slab once
+    auto fr = [&](auto *&p) {
+        if (q.slab && (const char *)p >= (const char *)q.slab &&
+            (const char *)p < (const char *)q.slab + q.slab_bytes)
+            p = nullptr;
+        else
+            dfree(c, p);
+    };
     for (auto &t : q.r) {
-        dfree(c, t.S_dev);
-        dfree(c, t.L_dev);
-        dfree(c, t.seg_id);
-        dfree(c, t.seg_first);
-        for (auto &l : t.link) dfree(c, l);
+        fr(t.S_dev);
+        fr(t.L_dev);
+        fr(t.seg_id);
+        fr(t.seg_first);
+        for (auto &l : t.link) fr(l);
         t.link.clear();
-        dfree(c, t.w);
-        dfree(c, t.off);
-        dfree(c, t.msg);
-        dfree(c, t.down);
-        dfree(c, t.mult);
-        dfree(c, t.lgid);
-        dfree(c, t.loff);
-        dfree(c, t.lw);
-        dfree(c, t.lseg_first);
+        fr(t.w);
+        fr(t.off);
+        fr(t.msg);
+        fr(t.down);
+        fr(t.mult);
+        fr(t.lgid);
+        fr(t.loff);
+        fr(t.lw);
+        fr(t.lseg_first);
     }
+    dfree_bytes(c, q.slab);
+    q.slab = nullptr;
+    q.slab_bytes = 0;
     q.summarized = false;
 }
 
@@ -770,6 +782,47 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
     Ctx &c = q.ctx();
     query_free_summary(c, q);
     cudaError_t e = cudaSuccess;
+    // every per-relation array below comes from one slab (a bump arena on
+    // the context while this call runs), unless the context already bumps
+    // from an arena of its own
+    struct ArenaScope {
+        Ctx &c;
+        bool active = false;
+        char *a;
+        size_t size, used;
+        bool on;
+        explicit ArenaScope(Ctx &cc) : c(cc), a(cc.arena), size(cc.arena_size), used(cc.arena_used), on(cc.arena_on) {}
+        void set(void *slab, size_t bytes) {
+            active = true;
+            c.arena = (char *)slab;
+            c.arena_size = bytes;
+            c.arena_used = 0;
+            c.arena_on = true;
+        }
+        ~ArenaScope() {
+            if (!active) return;
+            c.arena = a;
+            c.arena_size = size;
+            c.arena_used = used;
+            c.arena_on = on;
+        }
+    } arena_scope(c);
+    if (!c.arena_on) {
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        size_t sb = 0;
+        for (const QRel &t : q.r) {
+            const size_t G = (size_t)std::max<int64_t>(t.F->G, 1);
+            sb += t.children.size() * al(4 * G);                       // links
+            sb += 5 * al(8 * G) + al(4 * G) + al(4);                   // w, off, loff, lw, mult; lgid; L_dev
+            if (t.parent >= 0)
+                sb += 2 * al(8 * G) + al(4 * G) + 2 * al(4 * (G + 1)) + al(4);   // msg, down; seg_id; seg_first, lseg_first; S_dev
+        }
+        void *slab = nullptr;
+        e = dalloc_bytes(c, &slab, sb);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+        q.slab = slab;
+        q.slab_bytes = sb;
+    }
     // one block of scratch for the whole summary: every relation's lookback
     // state, every dense link table, every child's down accumulators, |Q|
     std::vector<int64_t> st_off(q.k), dense_off(q.k, -1), dense_range(q.k, 0), acc_off(q.k, -1);
@@ -813,6 +866,7 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
     } while (0)
     {
         TRY(dalloc_bytes(c, (void **)&scratch, bytes));
+        if (q.slab) arena_scope.set(q.slab, q.slab_bytes);   // the arrays from here on
         TRY(cudaMemsetAsync(scratch, 0, zero_end, c.stream));
         if (dense_end > zero_end) TRY(cudaMemsetAsync(scratch + zero_end, 0xFF, dense_end - zero_end, c.stream));
         if (bytes > dense_end) TRY(cudaMemsetAsync(scratch + dense_end, 0, bytes - dense_end, c.stream));
