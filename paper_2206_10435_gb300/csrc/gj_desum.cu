@@ -231,18 +231,45 @@ k_expand_write(ExpandSpec s, const uint32_t *F_dev, const uint32_t *__restrict__
     }
 }
 
+// first index h in [a, b) with key(h) > x (key non-decreasing), by one warp:
+// each round the 32 lanes probe 32 evenly spaced points and the interval
+// shrinks to the gap between two of them (about log32 of the length rounds)
+template <class F>
+__device__ __forceinline__ uint32_t warp_first_greater(uint32_t a, uint32_t b, uint64_t x, F key) {
+    const int lane = threadIdx.x & 31;
+    while (b - a > 32) {
+        const uint32_t step = (b - a + 31) / 32;
+        const uint32_t p = a + lane * step;   // lane 0 probes a
+        const bool gt = p < b && key(p) > x;
+        const uint32_t m = __ballot_sync(0xffffffffu, gt);
+        // the answer lies in (probe of the last lane not greater, probe of the first greater]
+        const int f = m ? __ffs((int)m) - 1 : 32;   // first probing lane with key > x
+        if (f == 0) return a;                        // key(a) > x
+        if (f == 32) {                               // none greater: past the last probe inside
+            a += ((b - 1 - a) / step) * step + 1;
+        } else {                                     // between probes f - 1 and f
+            b = a + (uint32_t)f * step;
+            a += (uint32_t)(f - 1) * step + 1;
+        }
+    }
+    const uint32_t p = a + lane;
+    const bool gt = p < b && key(p) > x;
+    const uint32_t m = __ballot_sync(0xffffffffu, gt);
+    return m ? a + (uint32_t)(__ffs((int)m) - 1) : b;
+}
+
 __global__ void k_root_range(const uint64_t *loff, const uint64_t *lw, const uint32_t *L_dev,
                              uint64_t row0, uint64_t row_end, uint32_t *out, uint32_t *F_dev) {
-    // live root groups h with [loff, loff + lw) overlapping [row0, row_end)
+    // live root groups h with [loff, loff + lw) overlapping [row0, row_end):
+    // one warp, two searches
     const uint32_t L = *L_dev;
-    uint32_t a = 0, b = L;
-    while (a < b) { uint32_t m = a + ((b - a) >> 1); if (loff[m] + lw[m] > row0) b = m; else a = m + 1; }
-    uint32_t lo = a;
-    a = lo; b = L;
-    while (a < b) { uint32_t m = a + ((b - a) >> 1); if (loff[m] > row_end - 1) b = m; else a = m + 1; }
-    out[0] = lo;
-    out[1] = a;
-    *F_dev = a - lo;
+    const uint32_t lo = warp_first_greater(0u, L, row0, [&](uint32_t h) { return loff[h] + lw[h]; });
+    const uint32_t hi = warp_first_greater(lo, L, row_end - 1, [&](uint32_t h) { return loff[h]; });
+    if (threadIdx.x == 0) {
+        out[0] = lo;
+        out[1] = hi;
+        *F_dev = hi - lo;
+    }
 }
 
 __global__ void k_root_init(const uint32_t *lo_dev, const uint32_t *F_dev, const uint32_t *lgid,
@@ -343,7 +370,7 @@ cudaError_t expand(QueryState &q, uint64_t row0, uint64_t row_end, int depth, bo
     Frontier cur;
     FrontierHold hold_cur{c, cur};
     GJ_CUDA_TRY(frontier_alloc(c, cur, cap, 1, keep_last && depth == 1));
-    k_root_range<<<1, 1, 0, c.stream>>>(root.loff, root.lw, root.L_dev, row0, row_end, rr,
+    k_root_range<<<1, 32, 0, c.stream>>>(root.loff, root.lw, root.L_dev, row0, row_end, rr,
                                         cur.F_dev); c.launches++;
     k_root_init<<<grid_for(c, cap), DT, 0, c.stream>>>(rr, cur.F_dev, root.lgid, root.loff,
                                                       root.F->gstart, cur.A, cur.W, cur.grp[0],
