@@ -633,7 +633,26 @@ def run_serve(a, rank, world, local):
         if not warm:
             sweep.append(st)
     clk = clocks.stop()
-    best = max((s.get("qps") or 0) for s in sweep)
+    # every rank serves its own stream at each offered rate (weak scaling):
+    # the job's served rate at a step is the sum over ranks; the latencies
+    # reported are the worst rank's
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        q = torch.tensor([s.get("qps") or 0.0 for s in sweep], dtype=torch.float64, device=dev)
+        dist.all_reduce(q)
+        lat_keys = ["p50_first_chunk_ms", "p99_first_chunk_ms", "p50_last_chunk_ms", "p99_last_chunk_ms"]
+        lat = torch.tensor([[s.get(k) or 0.0 for k in lat_keys] for s in sweep], dtype=torch.float64, device=dev)
+        dist.all_reduce(lat, op=dist.ReduceOp.MAX)
+        for i, s in enumerate(sweep):
+            s["qps_all_ranks"] = float(q[i].item())
+            s["offered_qps_all_ranks"] = s["offered_qps"] * world
+            for j, k in enumerate(lat_keys):
+                s[k + "_worst_rank"] = float(lat[i, j].item())
+        best = max(s["qps_all_ranks"] for s in sweep)
+        dist.destroy_process_group()
+    else:
+        best = max((s.get("qps") or 0) for s in sweep)
     out = {"metric": "served queries/s (continuous admission, resident factors)",
            "value": best, "unit": "queries/s", "n_gpus": world, "steps": len(rates),
            "warmup": n_warm, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -644,6 +663,8 @@ def run_serve(a, rank, world, local):
                                    f"the result's first {a.serve_max_rows or 'all'} rows streamed "
                                    f"in 2^{a.serve_chunk_log2}-row chunks per request; 150 GB HBM budget"),
                       "slots": a.slots, "engine": a.serve_engine, "factor_build_s": warm_s,
+                      "parallelism": (f"{world} rank(s), one per GPU, each serving its own stream at "
+                                      "every offered rate; served q/s summed over ranks"),
                       "l2": "not flushed: the requests of a stream share L2, as in service"},
            "sweep": sweep, "clocks": clk}
     if rank == 0:
