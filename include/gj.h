@@ -128,11 +128,19 @@ gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
  * used only while they take at most 512 MiB, else lists).  The triples and
  * their order are the same either way.  Takes effect at the next
  * gj_summarize.
+ * GJ_OPT_DOWN_COMBINE: how the downward pass (Algorithm 2's messages back
+ * down the tree) adds the contributions of a relation's groups to a
+ * child's down message: 0 (default) combines them per thread block in
+ * shared memory first where the links to that child are not in key order
+ * (so skewed keys do not serialise on one address), 1 never, 2 for every
+ * child.  The sums are exact integers: the summary is the same either way.
+ * Takes effect at the next gj_summarize.
  * Unknown options and values outside these ranges return GJ_ERR_INVALID
  * and change nothing; a NULL ctx returns GJ_ERR_INVALID.
  */
 #define GJ_OPT_EMIT_ROWS_PER_THREAD 1
 #define GJ_OPT_TRIANGLE_INTERSECT 2
+#define GJ_OPT_DOWN_COMBINE 6
 gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value);
 
 /*

@@ -8,6 +8,11 @@ bits), so a later batch of the same shape skips the timing.
 
 Desummarisation: the emit kernel's rows per thread, timed on a real window
 of the query and cached by the GPU and the result's shape (tune_emit).
+
+The summary: how the downward pass combines contributions to a child's down
+message (GJ_OPT_DOWN_COMBINE) for a join tree, or how the 3-cycle finds its
+group triples (GJ_OPT_TRIANGLE_INTERSECT), timed on the query's own
+gj_summarize and cached by the GPU and the query's shape (tune_summary).
 """
 from __future__ import annotations
 
@@ -128,3 +133,77 @@ def tune_emit(ctx, query, window: int = 1 << 24, reps: int = 3, cache_path: str 
         json.dump(cache, open(tmp, "w"), indent=1)
         os.replace(tmp, cache_path)
     return dict(entry, cached=False)
+
+
+# ---------------------------------------------------------------- summary
+def summary_signature(query, gpu_name: str, kind: str) -> str:
+    groups = [max(1, g) for g in query.n_groups]
+    g2 = "-".join(str(int(round(math.log2(g)))) for g in groups)
+    tree = "-".join(str(p) for p in query.parent)
+    return f"{gpu_name}|summary|{kind}|rel{query.n_rel}|groups2^{g2}|parents{tree}"
+
+
+def _load_cache(path, use):
+    if use and os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store_cache(path, cache):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    json.dump(cache, open(tmp, "w"), indent=1)
+    os.replace(tmp, path)
+
+
+def tune_summary(ctx, query, triangle: bool = False, reps: int = 3, cache_path: str = DEFAULT_CACHE,
+                 use_cache: bool = True) -> dict:
+    """Times gj_summarize of the query for every choice of the summary's
+    option -- GJ_OPT_TRIANGLE_INTERSECT (1 sorted lists, 2 bitmaps) for the
+    3-cycle, GJ_OPT_DOWN_COMBINE (0 by key order, 1 never, 2 always)
+    otherwise -- and leaves the fastest set on the context.  Every choice
+    gives the same summary; the timings and the choice are returned."""
+    import torch
+    from . import gj
+    opt, cands, name = ((gj.GJ_OPT_TRIANGLE_INTERSECT, (1, 2), "triangle_intersect") if triangle
+                        else (gj.GJ_OPT_DOWN_COMBINE, (0, 1, 2), "down_combine"))
+    gpu = torch.cuda.get_device_name(ctx.device)
+    key = summary_signature(query, gpu, name)
+    cache = _load_cache(cache_path, use_cache)
+    if use_cache and key in cache:
+        ctx.set_option(opt, int(cache[key][name]))
+        return dict(cache[key], cached=True)
+    stream = ctx.stream
+    times, totals = {}, {}
+    for v in cands:
+        ctx.set_option(opt, v)
+        totals[v] = _summarize_or_sat(query, gj)    # warm-up, and the result to compare
+        stream.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            _summarize_or_sat(query, gj)
+        t1.record(stream)
+        t1.synchronize()
+        times[v] = t0.elapsed_time(t1) / reps
+    if len(set(totals.values())) != 1:
+        raise RuntimeError(f"summary options disagree on |Q|: {totals}")
+    best = min(times, key=times.get)
+    ctx.set_option(opt, best)
+    entry = {name: best, "ms": times[best], "candidates_ms": {str(k): v for k, v in times.items()}}
+    if use_cache:
+        cache[key] = entry
+        _store_cache(cache_path, cache)
+    return dict(entry, cached=False)
+
+
+def _summarize_or_sat(query, gj):
+    try:
+        return query.summarize()
+    except gj.GJError as e:
+        if e.status != gj.GJ_ERR_OVERFLOW:
+            raise
+        return gj.SAT

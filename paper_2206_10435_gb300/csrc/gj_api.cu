@@ -203,6 +203,11 @@ gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value) {
         ctx->s.c.tri_mode = (int)value;
         return GJ_OK;
     }
+    if (option == GJ_OPT_DOWN_COMBINE) {
+        if (value < 0 || value > 2) return GJ_ERR_INVALID;
+        ctx->s.c.down_combine = (int)value;
+        return GJ_OK;
+    }
     if (option == GJ_OPT_SPIN_LIMIT) {
         if (value < 0 || value > (int64_t)SPIN_LIMIT) return GJ_ERR_INVALID;
         ctx->s.c.spin_limit = value == 0 ? SPIN_LIMIT : (uint32_t)value;
@@ -630,6 +635,7 @@ gj_status gj_query_set_stream(gj_query *q, void *cuda_stream) {
         o->num_sms = base.num_sms;
         o->emit_rpt = base.emit_rpt;
         o->tri_mode = base.tri_mode;
+        o->down_combine = base.down_combine;
         if (cudaMalloc((void **)&o->err, 16) != cudaSuccess ||
             cudaMallocHost((void **)&o->pinned, 1 << 16) != cudaSuccess) {
             cudaGetLastError();

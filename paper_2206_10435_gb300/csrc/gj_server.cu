@@ -317,6 +317,8 @@ gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, ui
         }
         x->num_sms = ctx->s.c.num_sms;
         x->emit_rpt = ctx->s.c.emit_rpt;
+        x->tri_mode = ctx->s.c.tri_mode;
+        x->down_combine = ctx->s.c.down_combine;
         x->stream = s;
         if (st == GJ_OK && (cudaMalloc((void **)&x->err, 16) != cudaSuccess ||
                             cudaMallocHost((void **)&x->pinned, 1 << 16) != cudaSuccess)) {

@@ -981,7 +981,8 @@ gj_status summarize(QueryState &q, uint64_t *total_out) {
                 // leading factor columns: no combining needed
                 const std::vector<int> &sp = q.r[t.children[ci]].sep_cols_parent;
                 const std::vector<int> &ord = t.F->order;
-                d.agg[ci] = !(sp.size() <= ord.size() && std::equal(sp.begin(), sp.end(), ord.begin()));
+                const bool in_order = sp.size() <= ord.size() && std::equal(sp.begin(), sp.end(), ord.begin());
+                d.agg[ci] = c.down_combine == 2 || (c.down_combine == 0 && !in_order);
             }
             launch_down(c, grid_for(c, G), d);
             TRY(cudaGetLastError());

@@ -25,6 +25,7 @@ GJ_OK, GJ_ERR_INVALID, GJ_ERR_NOT_ACYCLIC, GJ_ERR_OOM, GJ_ERR_OVERFLOW, GJ_ERR_C
 GJ_REL_BORROW, GJ_REL_COPY, GJ_REL_HOST = 0, 1, 2
 GJ_OPT_EMIT_ROWS_PER_THREAD = 1
 GJ_OPT_TRIANGLE_INTERSECT = 2   # 0 chooses, 1 sorted lists, 2 bitmaps
+GJ_OPT_DOWN_COMBINE = 6         # downward pass: 0 combine where links are out of key order, 1 never, 2 always
 GJ_OPT_SPIN_LIMIT = 3           # failure injection: polls of the group scan's bounded wait
 GJ_OPT_TEST_STALL = 4           # failure injection: that wait runs out
 GJ_OPT_FAIL_ALLOC_AT = 5        # failure injection: the N-th device allocation fails
