@@ -135,12 +135,17 @@ gj_status gj_set_stream(gj_ctx *ctx, void *cuda_stream);
  * (so skewed keys do not serialise on one address), 1 never, 2 for every
  * child.  The sums are exact integers: the summary is the same either way.
  * Takes effect at the next gj_summarize.
+ * GJ_OPT_SLOT_ARENA: bytes of the bump arena each slot of a server created
+ * afterwards takes its requests' device memory from (default 512 MiB, 0 =
+ * none: every allocation goes to the slot's memory pool; at most 2^40).  A
+ * request that needs more continues in the pool; results are the same.
  * Unknown options and values outside these ranges return GJ_ERR_INVALID
  * and change nothing; a NULL ctx returns GJ_ERR_INVALID.
  */
 #define GJ_OPT_EMIT_ROWS_PER_THREAD 1
 #define GJ_OPT_TRIANGLE_INTERSECT 2
 #define GJ_OPT_DOWN_COMBINE 6
+#define GJ_OPT_SLOT_ARENA 7
 gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value);
 
 /*

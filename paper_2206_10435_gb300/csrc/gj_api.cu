@@ -208,6 +208,11 @@ gj_status gj_set_option(gj_ctx *ctx, int32_t option, int64_t value) {
         ctx->s.c.down_combine = (int)value;
         return GJ_OK;
     }
+    if (option == GJ_OPT_SLOT_ARENA) {
+        if (value < 0 || value > (1ll << 40)) return GJ_ERR_INVALID;
+        ctx->s.c.slot_arena = (size_t)value;
+        return GJ_OK;
+    }
     if (option == GJ_OPT_SPIN_LIMIT) {
         if (value < 0 || value > (int64_t)SPIN_LIMIT) return GJ_ERR_INVALID;
         ctx->s.c.spin_limit = value == 0 ? SPIN_LIMIT : (uint32_t)value;

@@ -59,6 +59,7 @@ struct Ctx {
     int emit_rpt = 4;                 // result rows per thread of the emit kernel (2, 4 or 8)
     int tri_mode = 0;                 // triangle intersection: 0 chooses, 1 sorted lists, 2 bitmaps
     int down_combine = 0;             // downward pass: 0 by key order, 1 never, 2 always
+    size_t slot_arena = (size_t)512 << 20;   // arena bytes of each server slot
     // failure injection (tests): polls before the group scan's bounded wait
     // gives up, whether tile 0 of that scan withholds its status (so the
     // wait runs out), and the stream-ordered allocation to fail (counted

@@ -32,11 +32,6 @@ gj_status desummarize(QueryState &q, uint64_t row0, uint64_t nrows, void *const 
 
 namespace {
 
-// device memory of one slot's requests, taken by bumping a pointer: a
-// request (summary, and each result chunk's temporaries) that needs more
-// continues in the slot's pool
-constexpr size_t SLOT_ARENA = (size_t)512 << 20;
-
 // Order-independent, position-dependent hash of a result chunk: the
 // xor over rows and columns of a 64-bit mix of (column, row, value).
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -327,13 +322,16 @@ gj_status gj_server_create(gj_ctx *ctx, int32_t n_slots, uint64_t hbm_budget, ui
         }
         if (x->err) cudaMemset(x->err, 0, 16);
         // the slot's arena, from its pool (so that admission counts it)
-        if (st == GJ_OK && SLOT_ARENA > 0) {
+        // (a request that needs more -- summary, and each result chunk's
+        // temporaries -- continues in the slot's pool)
+        const size_t arena = ctx->s.c.slot_arena;
+        if (st == GJ_OK && arena > 0) {
             void *a = nullptr;
-            cudaError_t e = x->pool ? cudaMallocFromPoolAsync(&a, SLOT_ARENA, x->pool, s)
-                                    : cudaMallocAsync(&a, SLOT_ARENA, s);
+            cudaError_t e = x->pool ? cudaMallocFromPoolAsync(&a, arena, x->pool, s)
+                                    : cudaMallocAsync(&a, arena, s);
             if (e == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess) {
                 x->arena = (char *)a;
-                x->arena_size = SLOT_ARENA;
+                x->arena_size = arena;
             } else {
                 cudaGetLastError();   // no arena: the slot allocates from its pool
             }

@@ -26,6 +26,7 @@ GJ_REL_BORROW, GJ_REL_COPY, GJ_REL_HOST = 0, 1, 2
 GJ_OPT_EMIT_ROWS_PER_THREAD = 1
 GJ_OPT_TRIANGLE_INTERSECT = 2   # 0 chooses, 1 sorted lists, 2 bitmaps
 GJ_OPT_DOWN_COMBINE = 6         # downward pass: 0 combine where links are out of key order, 1 never, 2 always
+GJ_OPT_SLOT_ARENA = 7           # bytes of each server slot's bump arena (0: none)
 GJ_OPT_SPIN_LIMIT = 3           # failure injection: polls of the group scan's bounded wait
 GJ_OPT_TEST_STALL = 4           # failure injection: that wait runs out
 GJ_OPT_FAIL_ALLOC_AT = 5        # failure injection: the N-th device allocation fails

@@ -90,3 +90,65 @@ def test_native_server_alone_equals_mix():
         for x in q:
             ctx.release_relation(x)
     ctx.close()
+
+
+def _small_pool(n=8, seed=19):
+    """Chains of 2-4 tables with results of 10^2..3*10^4 rows (the oracle
+    materialises them whole)."""
+    rng = np.random.default_rng(seed)
+    qs = []
+    for i in range(n):
+        k = int(rng.integers(2, 5))
+        rows = rng.integers(50, 800, size=k)
+        doms = rng.integers(20, 300, size=k + 1)
+        s = float(rng.uniform(0, 1.2))
+        qs.append(G.chain_query(f"a{i}", rows, doms, [s] * (k + 1), np.int64 if i % 2 else np.int32,
+                                3000 + i))
+    return qs
+
+
+@pytest.mark.parametrize("arena", [0, 1 << 16, 1 << 22])
+def test_slot_arena_sizes_give_the_same_results(arena):
+    """Each slot takes its requests' device memory from a bump arena: none
+    (every allocation from the slot's pool), one too small for any request
+    (the summary and every chunk continue in the pool part way), and one
+    that holds small requests whole.  Sizes, streamed rows and their hashes
+    equal the oracle's, whatever the arena."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10435_gb300 import gj
+    ctx = gj.Context(0, torch.cuda.Stream())
+    ctx.set_option(gj.GJ_OPT_SLOT_ARENA, arena)
+    pool = _small_pool()
+    ref = [O.count(q).total for q in pool]
+    ids = [gj.load_query(ctx, q) for q in pool]
+    chunk = 1 << 12
+    limit = 3 * chunk + 5
+    srv = gj.NativeServer(ctx, n_slots=4, chunk_rows=chunk, max_rows=limit)
+    picks = [i % len(ids) for i in range(48)]
+    res, _ = srv.run([ids[p] for p in picks], np.zeros(len(picks)))
+    srv.close()
+    hashes = {}
+    for q, qi in zip(pool, range(len(pool))):
+        j = O.join(q)
+        hashes[qi] = _hash_columns(O.columns(q, j.rowids[:min(limit, ref[qi])]))
+    for r, p in zip(res, picks):
+        assert r["status"] == gj.GJ_OK
+        assert r["total"] == ref[p] and r["rows"] == min(limit, ref[p])
+        assert r["hash"] == hashes[p]
+    for q in ids:
+        for x in q:
+            ctx.release_relation(x)
+    ctx.close()
+
+
+def test_slot_arena_option_range():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10435_gb300 import gj
+    ctx = gj.Context(0)
+    for bad in (-1, (1 << 40) + 1):
+        with pytest.raises(gj.GJError) as e:
+            ctx.set_option(gj.GJ_OPT_SLOT_ARENA, bad)
+        assert e.value.status == gj.GJ_ERR_INVALID
+    ctx.close()
