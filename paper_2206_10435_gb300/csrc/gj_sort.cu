@@ -8,8 +8,8 @@
 //     histogram of every digit in shared memory (warp-private bins, then
 //     global atomics); a tiny kernel turns them into bucket bases;
 //   * per digit, each CTA takes the next tile id from a global counter,
-//     ranks its 4096 keys with a warp-level multi-split (__match_any_sync
-//     peers, per-warp bins, no atomics), publishes its per-digit counts,
+//     ranks its 4096 keys with a warp-level multi-split (peers found by
+//     one ballot per digit bit, per-warp bins, no atomics), publishes its per-digit counts,
 //     finds each digit's global offset by decoupled lookback over the
 //     preceding tiles (bounded polls, ERRF_TIMEOUT on expiry), stages the
 //     tile in shared memory in digit order and scatters it so that
@@ -167,7 +167,14 @@ k_onesweep_t(const uint64_t *__restrict__ kin, PackSrc ps, const uint32_t *__res
         int64_t idx = wbase + i * 32 + lane;
         bool valid = idx < n;
         uint32_t d = valid ? (uint32_t)((k[i] >> shift) & 0xff) : 0x100u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        // lanes with the same digit (and validity): one ballot per bit
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; b++) {
+            const uint32_t bit = (d >> b) & 1u;
+            const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (valid && lane == leader) {
