@@ -40,8 +40,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gj", choices=["gj", "reference"])
     p.add_argument("--workload", default="chain5_zipf",
-                   choices=["chain5_zipf", "chain3_uniform", "star_poisson", "triangle", "batch",
-                            "serve", "reuse", "sensitivity"])
+                   choices=["chain5_zipf", "chain3_uniform", "star_poisson", "triangle", "square",
+                            "batch", "serve", "reuse", "sensitivity"])
     p.add_argument("--rates", default="100,200,500,1000,2000,5000,10000",
                    help="serve workload: offered arrival rates (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
@@ -81,6 +81,10 @@ def workload_name(a):
         return ("triangle: cyclic R(A,B) S(B,C) T(C,A), 10^6 rows/table, int32 keys uniform over "
                 "[0,1000), int64 payload/table, one-cluster junction tree, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
+    if a.workload == "square":
+        return ("square: cyclic R0(A,B) R1(B,C) R2(C,D) R3(D,A), 10^5 rows/table, int32 keys "
+                "uniform over [0,1000), int64 payload/table, one maxclique {A,B,C,D} joined "
+                f"group-wise relation by relation, desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "star_poisson":
         return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
                 "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "
@@ -107,6 +111,8 @@ def make_query(a, rank):
         return G.star_poisson(seed=G.SEED_BASE + 2 + 1000 * rank)
     if a.workload == "triangle":
         return G.triangle_query(G.SEED_BASE + 5 + 1000 * rank, [10**6] * 3, domain=1000)
+    if a.workload == "square":
+        return G.cyclic_query(G.SEED_BASE + 7 + 1000 * rank, "square", [10**5] * 4, domain=1000)
     return G.chain5_zipf(seed=G.SEED_BASE + 1 + 1000 * rank, rows=a.rows, domain=a.domain,
                          s=a.zipf)
 
@@ -280,6 +286,7 @@ def reduce_over_ranks(dist, elapsed_ms: float, rows: int, device):
 
 
 DEFAULT_SAMPLE = {"chain5_zipf": 5000, "chain3_uniform": 10**4, "star_poisson": 250000, "triangle": 2500,
+                  "square": 500,
                   "batch": 0, "serve": 0, "reuse": 0, "sensitivity": 0}
 
 
@@ -429,9 +436,10 @@ def main():
     phase_rooflines = {}
     for name, b, ms in (("factor_build", build_b, phase["build_ms"]),
                         ("summary", summ_b, phase["summary_ms"])):
-        if name == "summary" and a.workload == "triangle":
-            # the cyclic join's summary is its maxclique potential (an
-            # intersection of sorted segments), not a pass over groups
+        if name == "summary" and a.workload in ("triangle", "square"):
+            # a cyclic join's summary is its maxclique potential (segment
+            # intersections for the 3-cycle, group-wise joins otherwise),
+            # not a pass over groups
             phase_rooflines[name] = {"algorithmic_bytes": None, "ms": ms, "achieved": None,
                                      "unit": "GB/s", "frac": None,
                                      "note": "maxclique potential: no per-group byte count"}

@@ -51,6 +51,12 @@ struct StepSpec {
     const int32_t *dst_key[MAX_KEYS];   // relation j's group keys of the attribute
     int64_t G;                          // relation j's groups
     const uint32_t *item_grp[MAX_REL];  // the items' groups, by relation
+    // optional: the groups whose first shared column has value range_mn + v
+    // are [range_lo[v], range_lo[v + 1]) (v < range_n); the searches then
+    // run inside that range
+    const uint32_t *range_lo;
+    int32_t range_mn;
+    uint32_t range_n;
     uint32_t *err;
 };
 
@@ -64,17 +70,44 @@ __device__ __forceinline__ int cmp_group(const StepSpec &s, const int32_t (&want
     return 0;
 }
 
+// range_lo of a step: relation j's groups are sorted by their first shared
+// column, so range_lo[x] is the first group whose value is >= mn + x (one
+// binary search per value; x = nv gives G)
+__global__ void k_cyc_ranges(const int32_t *__restrict__ col, int64_t G, int32_t mn, uint32_t nv,
+                             uint32_t *lo) {
+    for (int64_t x = (int64_t)blockIdx.x * CT + threadIdx.x; x <= (int64_t)nv; x += (int64_t)gridDim.x * CT) {
+        const int64_t want = (int64_t)mn + x;
+        int64_t a = 0, b = G;
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if ((int64_t)col[m] < want) a = m + 1; else b = m;
+        }
+        lo[x] = (uint32_t)a;
+    }
+}
+
 __global__ void k_cyc_count(StepSpec s, int64_t F, uint64_t *cnt, uint32_t *lo_out) {
     for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < F; i += (int64_t)gridDim.x * CT) {
         int32_t want[MAX_KEYS];
         for (int c = 0; c < s.nshared; c++) want[c] = s.src_key[c][s.item_grp[s.src_pos[c]][i]];
-        int64_t a = 0, b = s.G;   // first group >= want
+        int64_t a = 0, hi = s.G;
+        if (s.range_lo) {
+            const int64_t v = (int64_t)want[0] - (int64_t)s.range_mn;
+            if (v < 0 || v >= (int64_t)s.range_n) {   // no group has that value
+                cnt[i] = 0;
+                lo_out[i] = 0;
+                continue;
+            }
+            a = s.range_lo[v];
+            hi = s.range_lo[v + 1];
+        }
+        int64_t b = hi;           // first group >= want
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if (cmp_group(s, want, m) < 0) a = m + 1; else b = m;
         }
         const int64_t lo = a;
-        b = s.G;                  // first group > want
+        b = hi;                   // first group > want
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if (cmp_group(s, want, m) <= 0) a = m + 1; else b = m;
@@ -88,11 +121,30 @@ struct OutGrp {
     uint32_t *g[MAX_REL];
 };
 
-// output slot o belongs to the last item whose exclusive offset is <= o
+// tile_first[t] = the item owning output slot t * WT (an item owns slots
+// [excl, excl + cnt)); one scatter over the items with slots
+constexpr int64_t WT = 1024;
+
+__global__ void k_cyc_tile_first(int64_t F, const uint64_t *__restrict__ cnt,
+                                 const uint64_t *__restrict__ excl, uint32_t *tile_first) {
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < F; i += (int64_t)gridDim.x * CT) {
+        const uint64_t c = cnt[i];
+        if (c == 0) continue;
+        const uint64_t lo = excl[i], hi = lo + c;
+        for (uint64_t t = (lo + WT - 1) / WT; t * WT < hi; t++) tile_first[t] = (uint32_t)i;
+    }
+}
+
+// output slot o belongs to the last item whose exclusive offset is <= o;
+// searched between the owners of its tile's first slot and of the next
+// tile's (items without slots lie between them too)
 __global__ void k_cyc_write(StepSpec s, int64_t F, const uint64_t *__restrict__ excl,
-                            const uint32_t *__restrict__ lo_in, int64_t Fout, OutGrp out) {
+                            const uint32_t *__restrict__ lo_in, int64_t Fout,
+                            const uint32_t *__restrict__ tile_first, OutGrp out) {
+    const int64_t tiles = (Fout + WT - 1) / WT;
     for (int64_t o = (int64_t)blockIdx.x * CT + threadIdx.x; o < Fout; o += (int64_t)gridDim.x * CT) {
-        int64_t a = 0, b = F;
+        const int64_t t = o / WT;
+        int64_t a = tile_first[t], b = t + 1 < tiles ? (int64_t)tile_first[t + 1] + 1 : F;
         while (a < b) {
             const int64_t m = (a + b) >> 1;
             if (excl[m] <= (uint64_t)o) a = m + 1; else b = m;
@@ -261,6 +313,22 @@ gj_status cyc_summarize(QueryState &q, uint64_t *total_out) {
             TRY(tmp.alloc(&excl, F));
             TRY(tmp.alloc(&lo, F));
             TRY(tmp.alloc(&tot, 1));
+            // the value ranges of relation j's first shared column, when
+            // small next to its groups
+            {
+                const int col0 = t.sep_cols[0];
+                const int64_t nv = (int64_t)t.R->kmax[col0] - (int64_t)t.R->kmin[col0] + 1;
+                if (t.F->G > 0 && nv <= (1ll << 26) && nv <= 4 * t.F->G + 4096) {
+                    uint32_t *rl = nullptr;
+                    TRY(tmp.alloc(&rl, nv + 1));
+                    k_cyc_ranges<<<grid_of(c, nv + 1), CT, 0, c.stream>>>(s.dst_key[0], t.F->G, t.R->kmin[col0],
+                                                                         (uint32_t)nv, rl); c.launches++;
+                    TRY(cudaGetLastError());
+                    s.range_lo = rl;
+                    s.range_mn = t.R->kmin[col0];
+                    s.range_n = (uint32_t)nv;
+                }
+            }
             uint64_t Fout = 0;
             if (F > 0) {
                 k_cyc_count<<<grid_of(c, F), CT, 0, c.stream>>>(s, F, cnt, lo); c.launches++;
@@ -283,7 +351,11 @@ gj_status cyc_summarize(QueryState &q, uint64_t *total_out) {
             if (Fout > 0) {
                 OutGrp og{};
                 for (int p = 0; p <= j; p++) og.g[p] = nxt[p];
-                k_cyc_write<<<grid_of(c, (int64_t)Fout), CT, 0, c.stream>>>(s, F, excl, lo, (int64_t)Fout, og); c.launches++;
+                uint32_t *tf = nullptr;
+                const int64_t tiles = ((int64_t)Fout + WT - 1) / WT;
+                TRY(tmp.alloc(&tf, tiles));
+                k_cyc_tile_first<<<grid_of(c, F), CT, 0, c.stream>>>(F, cnt, excl, tf); c.launches++;
+                k_cyc_write<<<grid_of(c, (int64_t)Fout), CT, 0, c.stream>>>(s, F, excl, lo, (int64_t)Fout, tf, og); c.launches++;
             }
             for (auto &g : cur) dfree(c, g);
             cur = nxt;

@@ -106,3 +106,15 @@ def test_tree_only_calls_rejected(ctx):
             call()
         assert e.value.status == gj.GJ_ERR_INVALID
     run.close()
+
+
+@pytest.mark.parametrize("spread", [1, -7, 1000003])
+def test_key_ranges_wide_narrow_and_negative(ctx, spread):
+    """The count step narrows its searches through a table over the first
+    shared column's value range when that range is small next to the groups;
+    keys stretched far apart (no table) or shifted negative give the same
+    rows as the oracle."""
+    q = G.cyclic_query(8200 + abs(spread) % 97, "pentagon", [220, 240, 260, 280, 300], domain=11, s=0.4)
+    for R in q.relations:
+        R.keys[:] = [(k.astype(np.int64) * spread - (5 if spread < 0 else 0)).astype(np.int32) for k in R.keys]
+    assert cyclic_parity(ctx, q, windows=[(5, 999)]) > 0
