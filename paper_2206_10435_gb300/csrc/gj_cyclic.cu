@@ -51,12 +51,15 @@ struct StepSpec {
     const int32_t *dst_key[MAX_KEYS];   // relation j's group keys of the attribute
     int64_t G;                          // relation j's groups
     const uint32_t *item_grp[MAX_REL];  // the items' groups, by relation
-    // optional: the groups whose first shared column has value range_mn + v
-    // are [range_lo[v], range_lo[v + 1]) (v < range_n); the searches then
-    // run inside that range
+    // optional: a table over the first range_cols (1 or 2) shared columns'
+    // values: the groups whose values are range_mn[c] + v_c are
+    // [range_lo[x], range_lo[x + 1]), x = v_0 (* range_nv[1] + v_1); when
+    // the table covers every shared column that range is the answer, else
+    // the searches run inside it
     const uint32_t *range_lo;
-    int32_t range_mn;
-    uint32_t range_n;
+    int range_cols;
+    int32_t range_mn[2];
+    uint32_t range_nv[2];
     uint32_t *err;
 };
 
@@ -70,17 +73,32 @@ __device__ __forceinline__ int cmp_group(const StepSpec &s, const int32_t (&want
     return 0;
 }
 
-// range_lo of a step: relation j's groups are sorted by their first shared
-// column, so range_lo[x] is the first group whose value is >= mn + x (one
-// binary search per value; x = nv gives G)
-__global__ void k_cyc_ranges(const int32_t *__restrict__ col, int64_t G, int32_t mn, uint32_t nv,
-                             uint32_t *lo) {
-    for (int64_t x = (int64_t)blockIdx.x * CT + threadIdx.x; x <= (int64_t)nv; x += (int64_t)gridDim.x * CT) {
-        const int64_t want = (int64_t)mn + x;
-        int64_t a = 0, b = G;
-        while (a < b) {
-            const int64_t m = (a + b) >> 1;
-            if ((int64_t)col[m] < want) a = m + 1; else b = m;
+// range_lo of a step: relation j's groups are sorted by their shared columns
+// first, so range_lo[x] is the first group whose leading range_cols values
+// are >= the tuple that x encodes (one binary search per x; x = the table's
+// size gives G)
+__global__ void k_cyc_ranges(StepSpec s, int64_t nx, uint32_t *lo) {
+    for (int64_t x = (int64_t)blockIdx.x * CT + threadIdx.x; x <= nx; x += (int64_t)gridDim.x * CT) {
+        int32_t want[2] = {0, 0};
+        if (s.range_cols == 2) {
+            want[0] = s.range_mn[0] + (int32_t)(x / s.range_nv[1]);
+            want[1] = s.range_mn[1] + (int32_t)(x % s.range_nv[1]);
+        } else {
+            want[0] = s.range_mn[0] + (int32_t)x;
+        }
+        int64_t a = 0, b = s.G;
+        if (x < nx) {
+            while (a < b) {
+                const int64_t m = (a + b) >> 1;
+                int cmp = 0;
+                for (int c = 0; c < s.range_cols && cmp == 0; c++) {
+                    const int32_t v = s.dst_key[c][m];
+                    cmp = v < want[c] ? -1 : (v > want[c] ? 1 : 0);
+                }
+                if (cmp < 0) a = m + 1; else b = m;
+            }
+        } else {
+            a = s.G;
         }
         lo[x] = (uint32_t)a;
     }
@@ -92,14 +110,25 @@ __global__ void k_cyc_count(StepSpec s, int64_t F, uint64_t *cnt, uint32_t *lo_o
         for (int c = 0; c < s.nshared; c++) want[c] = s.src_key[c][s.item_grp[s.src_pos[c]][i]];
         int64_t a = 0, hi = s.G;
         if (s.range_lo) {
-            const int64_t v = (int64_t)want[0] - (int64_t)s.range_mn;
-            if (v < 0 || v >= (int64_t)s.range_n) {   // no group has that value
+            int64_t x = 0;
+            bool none = false;   // a value outside the relation's range: no group
+            for (int c = 0; c < s.range_cols; c++) {
+                const int64_t v = (int64_t)want[c] - (int64_t)s.range_mn[c];
+                none |= v < 0 || v >= (int64_t)s.range_nv[c];
+                x = x * (int64_t)s.range_nv[c] + v;
+            }
+            if (none) {
                 cnt[i] = 0;
                 lo_out[i] = 0;
                 continue;
             }
-            a = s.range_lo[v];
-            hi = s.range_lo[v + 1];
+            a = s.range_lo[x];
+            hi = s.range_lo[x + 1];
+            if (s.range_cols == s.nshared) {   // the table's range is the answer
+                cnt[i] = (uint64_t)(hi - a);
+                lo_out[i] = (uint32_t)a;
+                continue;
+            }
         }
         int64_t b = hi;           // first group >= want
         while (a < b) {
@@ -313,20 +342,30 @@ gj_status cyc_summarize(QueryState &q, uint64_t *total_out) {
             TRY(tmp.alloc(&excl, F));
             TRY(tmp.alloc(&lo, F));
             TRY(tmp.alloc(&tot, 1));
-            // the value ranges of relation j's first shared column, when
-            // small next to its groups
+            // a table over the value ranges of relation j's first one or
+            // two shared columns, when it stays small (at most 2^24 entries)
             {
-                const int col0 = t.sep_cols[0];
-                const int64_t nv = (int64_t)t.R->kmax[col0] - (int64_t)t.R->kmin[col0] + 1;
-                if (t.F->G > 0 && nv <= (1ll << 26) && nv <= 4 * t.F->G + 4096) {
+                constexpr int64_t MAX_RANGE = 1ll << 24;
+                int64_t nv[2] = {0, 0};
+                for (int ci = 0; ci < std::min(2, s.nshared); ci++) {
+                    const int col = t.sep_cols[ci];
+                    nv[ci] = (int64_t)t.R->kmax[col] - (int64_t)t.R->kmin[col] + 1;
+                }
+                int rc = std::min(2, s.nshared);
+                if (rc == 2 && nv[0] * nv[1] > MAX_RANGE) rc = 1;
+                if (rc == 1 && nv[0] > MAX_RANGE) rc = 0;
+                if (t.F->G > 0 && rc > 0) {
+                    const int64_t nx = rc == 2 ? nv[0] * nv[1] : nv[0];
+                    s.range_cols = rc;
+                    for (int ci = 0; ci < rc; ci++) {
+                        s.range_mn[ci] = t.R->kmin[t.sep_cols[ci]];
+                        s.range_nv[ci] = (uint32_t)nv[ci];
+                    }
                     uint32_t *rl = nullptr;
-                    TRY(tmp.alloc(&rl, nv + 1));
-                    k_cyc_ranges<<<grid_of(c, nv + 1), CT, 0, c.stream>>>(s.dst_key[0], t.F->G, t.R->kmin[col0],
-                                                                         (uint32_t)nv, rl); c.launches++;
+                    TRY(tmp.alloc(&rl, nx + 1));
+                    k_cyc_ranges<<<grid_of(c, nx + 1), CT, 0, c.stream>>>(s, nx, rl); c.launches++;
                     TRY(cudaGetLastError());
                     s.range_lo = rl;
-                    s.range_mn = t.R->kmin[col0];
-                    s.range_n = (uint32_t)nv;
                 }
             }
             uint64_t Fout = 0;
