@@ -224,6 +224,39 @@ __global__ void k_cyc_window(const uint64_t *A, uint64_t B, uint64_t row0, uint6
     out[1] = (uint32_t)(l - f + 1);
 }
 
+// the two-clique plan (cyc_split below): every item of the second clique
+// packed into one word over its attributes' values (fields from the low
+// end: field f at shift[f]); vals = the item's index
+struct ItemPack {
+    int nf;
+    const int32_t *key[8];      // group keys of the attribute's holder
+    const uint32_t *grp[8];     // the items' groups of that holder
+    int32_t mn[8];
+    int shift[8];
+};
+
+__global__ void k_cyc_pack_items(ItemPack p, int64_t n, uint64_t *keys, uint32_t *vals) {
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < n; i += (int64_t)gridDim.x * CT) {
+        uint64_t w = 0;
+        for (int f = 0; f < p.nf; f++)
+            w |= (uint64_t)((uint32_t)p.key[f][p.grp[f][i]] - (uint32_t)p.mn[f]) << p.shift[f];
+        keys[i] = w;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_cyc_gather(int64_t n, const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                             uint32_t *dst) {
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < n; i += (int64_t)gridDim.x * CT)
+        dst[i] = src[idx[i]];
+}
+
+__global__ void k_cyc_item_vals(int64_t n, const int32_t *__restrict__ key, const uint32_t *__restrict__ grp,
+                                int32_t *dst) {
+    for (int64_t i = (int64_t)blockIdx.x * CT + threadIdx.x; i < n; i += (int64_t)gridDim.x * CT)
+        dst[i] = key[grp[i]];
+}
+
 inline int grid_of(Ctx &c, int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, CT), (int64_t)c.num_sms * 16));
 }
@@ -233,6 +266,301 @@ cudaError_t read_u64(Ctx &c, const uint64_t *dev, uint64_t *host) {
     GJ_CUDA_TRY(cudaStreamSynchronize(c.stream));
     *host = c.pinned[0];
     return cudaSuccess;
+}
+
+// A step's optional table over the values of its first one or two shared
+// columns: their minima and value counts (n = 0: no table).
+struct RangeInfo {
+    int n = 0;
+    int32_t mn[2] = {0, 0};
+    int64_t nv[2] = {0, 0};
+};
+
+inline cudaError_t first_error(cudaError_t e) { return e != cudaSuccess ? e : cudaGetLastError(); }
+
+// One step of the group-wise join: the F items (their groups by item
+// position in cur[0 .. s.j - 1]) joined with the s.G candidates of position
+// s.j.  On success cur holds the new items (s.j + 1 arrays) and F their
+// number; GJ_ERR_OOM when they would be more than 2^31 or memory runs out.
+// Every array of the step is freed on every way out.
+gj_status cyc_step(Ctx &c, StepSpec s, const RangeInfo &ri, std::vector<uint32_t *> &cur, int64_t &F) {
+    constexpr int64_t MAX_RANGE = 1ll << 24;
+    Temps tmp(c);
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t x) {
+        note_cuda_error(x, __FILE__, __LINE__);
+        return x == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+    };
+    s.err = c.err;
+    for (int p = 0; p < s.j; p++) s.item_grp[p] = cur[p];
+    uint64_t *cnt = nullptr, *excl = nullptr, *tot = nullptr;
+    uint32_t *lo = nullptr;
+    if ((e = tmp.alloc(&cnt, F)) != cudaSuccess || (e = tmp.alloc(&excl, F)) != cudaSuccess ||
+        (e = tmp.alloc(&lo, F)) != cudaSuccess || (e = tmp.alloc(&tot, 1)) != cudaSuccess)
+        return fail(e);
+    int rc = std::min(ri.n, 2);
+    if (rc == 2 && ri.nv[0] * ri.nv[1] > MAX_RANGE) rc = 1;
+    if (rc == 1 && ri.nv[0] > MAX_RANGE) rc = 0;
+    if (s.G > 0 && rc > 0) {
+        const int64_t nx = rc == 2 ? ri.nv[0] * ri.nv[1] : ri.nv[0];
+        s.range_cols = rc;
+        for (int ci = 0; ci < rc; ci++) {
+            s.range_mn[ci] = ri.mn[ci];
+            s.range_nv[ci] = (uint32_t)ri.nv[ci];
+        }
+        uint32_t *rl = nullptr;
+        if ((e = tmp.alloc(&rl, nx + 1)) != cudaSuccess) return fail(e);
+        k_cyc_ranges<<<grid_of(c, nx + 1), CT, 0, c.stream>>>(s, nx, rl); c.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+        s.range_lo = rl;
+    }
+    uint64_t Fout = 0;
+    if (F > 0) {
+        k_cyc_count<<<grid_of(c, F), CT, 0, c.stream>>>(s, F, cnt, lo); c.launches++;
+        if ((e = first_error(cudaSuccess)) != cudaSuccess ||
+            (e = scan_u64_sat(c, cnt, nullptr, excl, F, tot, nullptr, nullptr)) != cudaSuccess ||
+            (e = read_u64(c, tot, &Fout)) != cudaSuccess)
+            return fail(e);
+    }
+    if (Fout > 0x7fffffffull) return GJ_ERR_OOM;   // more partial blocks than this path holds
+    std::vector<uint32_t *> nxt(s.j + 1, nullptr);
+    for (int p = 0; p <= s.j; p++)
+        if ((e = tmp.alloc(&nxt[p], (int64_t)Fout)) != cudaSuccess) return fail(e);
+    if (Fout > 0) {
+        OutGrp og{};
+        for (int p = 0; p <= s.j; p++) og.g[p] = nxt[p];
+        uint32_t *tf = nullptr;
+        const int64_t tiles = ((int64_t)Fout + WT - 1) / WT;
+        if ((e = tmp.alloc(&tf, tiles)) != cudaSuccess) return fail(e);
+        k_cyc_tile_first<<<grid_of(c, F), CT, 0, c.stream>>>(F, cnt, excl, tf); c.launches++;
+        k_cyc_write<<<grid_of(c, (int64_t)Fout), CT, 0, c.stream>>>(s, F, excl, lo, (int64_t)Fout, tf, og); c.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    }
+    for (uint32_t *g : nxt) tmp.keep(g);
+    for (auto &g : cur) dfree(c, g);
+    cur = nxt;
+    F = (int64_t)Fout;
+    return GJ_OK;
+}
+
+// The step adding relation j of the query to items over relations 0..j-1
+// (every shared attribute).
+StepSpec relation_step(QueryState &q, int j, RangeInfo &ri) {
+    const QRel &t = q.r[j];
+    StepSpec s{};
+    s.j = j;
+    s.nshared = (int)t.sep_cols.size();
+    for (int ci = 0; ci < s.nshared; ci++) {
+        const QRel &h = q.r[t.cyc_src_rel[ci]];
+        s.src_key[ci] = h.F->gkey + (int64_t)t.cyc_src_col[ci] * h.F->G;
+        s.src_pos[ci] = t.cyc_src_rel[ci];
+        s.dst_key[ci] = t.F->gkey + (int64_t)t.sep_cols[ci] * t.F->G;
+    }
+    s.G = t.F->G;
+    ri = RangeInfo{};
+    ri.n = std::min(2, s.nshared);
+    for (int ci = 0; ci < ri.n; ci++) {
+        const int col = t.sep_cols[ci];
+        ri.mn[ci] = t.R->kmin[col];
+        ri.nv[ci] = (int64_t)t.R->kmax[col] - (int64_t)t.R->kmin[col] + 1;
+    }
+    return s;
+}
+
+// The junction tree with two maxcliques, for queries of four or more
+// relations: clique 1 holds the attributes of relations 0 and 1, clique 2
+// those of relations 2 .. k-1, the separator their common attributes S (for
+// the 4-cycle R0(A,B) R1(B,C) R2(C,D) R3(D,A): cliques {A,B,C} and {C,D,A},
+// S = {A,C}, the chord A-C of its triangulation, Section 2.2).  Each
+// clique's potential is built group-wise as on one clique; clique 2's items
+// are then sorted by S (in V order) and the rest of its attributes (in V
+// order), and joined with clique 1's items on S.  No item ever spans both
+// sides before the join, so the paths a single clique would materialise
+// (every 3-path of a 4-cycle) never appear.  The blocks come out in V order:
+// clique 1's items in V order, each one's matches in the order of clique
+// 2's other attributes.  Taken when every relation of clique 2 after the
+// first joins the earlier ones of its clique on a leading run of its
+// shared columns (its factor is ordered by those first), S is not empty,
+// and clique 2's attributes pack into one 64-bit word; otherwise the query
+// stays on one clique (applied = false).
+gj_status cyc_split(QueryState &q, std::vector<uint32_t *> &blocks, int64_t &nb, bool &applied) {
+    applied = false;
+    const int k = q.k;
+    if (k < 4) return GJ_OK;
+    Ctx &c = q.ctx();
+    auto col_of = [&](int j, int32_t a) {
+        for (int cc = 0; cc < q.r[j].R->nk; cc++)
+            if (q.r[j].R->attr[cc] == a) return cc;
+        return -1;
+    };
+    auto holder = [&](int32_t a, int j0, int j1) {   // first relation of [j0, j1) holding a
+        for (int j = j0; j < j1; j++)
+            if (col_of(j, a) >= 0) return j;
+        return -1;
+    };
+    // S and clique 2's other attributes, both in V order
+    std::vector<int32_t> S, N;
+    for (size_t v = 0; v < q.var_rel.size(); v++) {
+        const int32_t a = q.r[q.var_rel[v]].R->attr[q.var_col[v]];
+        if (holder(a, 2, k) < 0) continue;
+        (holder(a, 0, 2) >= 0 ? S : N).push_back(a);
+    }
+    if (S.empty() || S.size() + N.size() > 8) return GJ_OK;
+    // clique 2's cascade: relation j joins relations 2..j-1 on a leading run
+    // of its shared columns
+    std::vector<int> lead(k, 0);
+    for (int j = 3; j < k; j++) {
+        const QRel &t = q.r[j];
+        int m = 0;
+        while (m < (int)t.sep_cols.size() && holder(t.R->attr[t.sep_cols[m]], 2, j) >= 0) m++;
+        for (int ci = m; ci < (int)t.sep_cols.size(); ci++)
+            if (holder(t.R->attr[t.sep_cols[ci]], 2, j) >= 0) return GJ_OK;
+        if (m == 0) return GJ_OK;
+        lead[j] = m;
+    }
+    // the sort key of clique 2's items: S then N, least significant last
+    ItemPack ip{};
+    std::vector<int32_t> fields(S);
+    fields.insert(fields.end(), N.begin(), N.end());
+    std::vector<int> fh(fields.size()), fc(fields.size());
+    int bits = 0;
+    for (int f = (int)fields.size() - 1; f >= 0; f--) {
+        fh[f] = holder(fields[f], 2, k);
+        fc[f] = col_of(fh[f], fields[f]);
+        const Relation &R = *q.r[fh[f]].R;
+        const uint32_t range = (uint32_t)((int64_t)R.kmax[fc[f]] - (int64_t)R.kmin[fc[f]]);
+        const int b = range == 0 ? 0 : 32 - __builtin_clz(range);
+        ip.shift[f] = bits;
+        ip.mn[f] = R.kmin[fc[f]];
+        bits += b;
+    }
+    if (bits > 64) return GJ_OK;
+    applied = true;
+
+    std::vector<uint32_t *> A(1, nullptr), Bi(1, nullptr), Bs;
+    std::vector<int32_t *> vS;
+    uint64_t *keys = nullptr;
+    uint32_t *vals = nullptr;
+    auto free_all = [&]() {
+        for (auto &g : A) dfree(c, g);
+        for (auto &g : Bi) dfree(c, g);
+        for (auto &g : Bs) dfree(c, g);
+        for (auto &v : vS) dfree(c, v);
+        dfree(c, keys);
+        dfree(c, vals);
+    };
+    auto cuda_fail = [&](cudaError_t x) {
+        note_cuda_error(x, __FILE__, __LINE__);
+        free_all();
+        return x == cudaErrorMemoryAllocation ? GJ_ERR_OOM : GJ_ERR_CUDA;
+    };
+    cudaError_t e = cudaSuccess;
+    gj_status st = GJ_OK;
+    // clique 1: relations 0 and 1
+    int64_t FA = q.r[0].F->G, FB = q.r[2].F->G;
+    if ((e = dalloc(c, &A[0], FA)) != cudaSuccess) return cuda_fail(e);
+    if (FA > 0) { k_cyc_iota<<<grid_of(c, FA), CT, 0, c.stream>>>(A[0], FA); c.launches++; }
+    {
+        RangeInfo ri;
+        StepSpec s1 = relation_step(q, 1, ri);
+        if ((st = cyc_step(c, s1, ri, A, FA)) != GJ_OK) { free_all(); return st; }
+    }
+    // clique 2: relations 2 .. k-1, at item positions 0 .. k-3
+    if ((e = dalloc(c, &Bi[0], FB)) != cudaSuccess) return cuda_fail(e);
+    if (FB > 0) { k_cyc_iota<<<grid_of(c, FB), CT, 0, c.stream>>>(Bi[0], FB); c.launches++; }
+    for (int j = 3; j < k; j++) {
+        const QRel &t = q.r[j];
+        StepSpec sb{};
+        sb.j = j - 2;
+        sb.nshared = lead[j];
+        RangeInfo ri;
+        ri.n = std::min(2, sb.nshared);
+        for (int ci = 0; ci < sb.nshared; ci++) {
+            const int32_t a = t.R->attr[t.sep_cols[ci]];
+            const int h = holder(a, 2, j);
+            sb.src_key[ci] = q.r[h].F->gkey + (int64_t)col_of(h, a) * q.r[h].F->G;
+            sb.src_pos[ci] = h - 2;
+            sb.dst_key[ci] = t.F->gkey + (int64_t)t.sep_cols[ci] * t.F->G;
+            if (ci < 2) {
+                ri.mn[ci] = t.R->kmin[t.sep_cols[ci]];
+                ri.nv[ci] = (int64_t)t.R->kmax[t.sep_cols[ci]] - (int64_t)t.R->kmin[t.sep_cols[ci]] + 1;
+            }
+        }
+        sb.G = t.F->G;
+        if ((st = cyc_step(c, sb, ri, Bi, FB)) != GJ_OK) { free_all(); return st; }
+    }
+    // clique 2's items in (S, N) order
+    Bs.assign(k - 2, nullptr);
+    if ((e = dalloc(c, &keys, FB)) != cudaSuccess || (e = dalloc(c, &vals, FB)) != cudaSuccess)
+        return cuda_fail(e);
+    for (int p = 0; p < k - 2; p++)
+        if ((e = dalloc(c, &Bs[p], FB)) != cudaSuccess) return cuda_fail(e);
+    if (FB > 0) {
+        ip.nf = (int)fields.size();
+        for (int f = 0; f < ip.nf; f++) {
+            ip.key[f] = q.r[fh[f]].F->gkey + (int64_t)fc[f] * q.r[fh[f]].F->G;
+            ip.grp[f] = Bi[fh[f] - 2];
+        }
+        k_cyc_pack_items<<<grid_of(c, FB), CT, 0, c.stream>>>(ip, FB, keys, vals); c.launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+        if (bits > 0 && (e = radix_sort_u64_u32(c, keys, vals, FB, bits)) != cudaSuccess) return cuda_fail(e);
+        for (int p = 0; p < k - 2; p++) {
+            k_cyc_gather<<<grid_of(c, FB), CT, 0, c.stream>>>(FB, Bi[p], vals, Bs[p]); c.launches++;
+        }
+    }
+    dfree(c, keys);
+    for (auto &g : Bi) dfree(c, g);
+    Bi.clear();
+    // S's values of the sorted items, the join's keys on clique 2's side
+    vS.assign(S.size(), nullptr);
+    for (size_t f = 0; f < S.size(); f++) {
+        if ((e = dalloc(c, &vS[f], FB)) != cudaSuccess) return cuda_fail(e);
+        if (FB > 0) {
+            k_cyc_item_vals<<<grid_of(c, FB), CT, 0, c.stream>>>(
+                FB, q.r[fh[f]].F->gkey + (int64_t)fc[f] * q.r[fh[f]].F->G, Bs[fh[f] - 2], vS[f]); c.launches++;
+        }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+    // the join of the cliques on S: clique 1's items (positions 0, 1) with
+    // the sorted items of clique 2 (position 2: the item's index)
+    {
+        StepSpec sf{};
+        sf.j = 2;
+        sf.nshared = (int)S.size();
+        RangeInfo ri;
+        ri.n = std::min<int>(2, sf.nshared);
+        for (int f = 0; f < sf.nshared; f++) {
+            const int h = holder(S[f], 0, 2);
+            sf.src_key[f] = q.r[h].F->gkey + (int64_t)col_of(h, S[f]) * q.r[h].F->G;
+            sf.src_pos[f] = h;
+            sf.dst_key[f] = vS[f];
+            if (f < 2) {
+                ri.mn[f] = ip.mn[f];
+                ri.nv[f] = (int64_t)q.r[fh[f]].R->kmax[fc[f]] - (int64_t)ip.mn[f] + 1;
+            }
+        }
+        sf.G = FB;
+        if ((st = cyc_step(c, sf, ri, A, FA)) != GJ_OK) { free_all(); return st; }
+    }
+    // the blocks' groups by relation
+    blocks.assign(k, nullptr);
+    blocks[0] = A[0];
+    blocks[1] = A[1];
+    A[0] = A[1] = nullptr;
+    for (int p = 0; p < k - 2; p++) {
+        if ((e = dalloc(c, &blocks[2 + p], FA)) != cudaSuccess) {
+            for (auto &g : blocks) dfree(c, g);
+            return cuda_fail(e);
+        }
+        if (FA > 0) { k_cyc_gather<<<grid_of(c, FA), CT, 0, c.stream>>>(FA, Bs[p], A[2], blocks[2 + p]); c.launches++; }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        for (auto &g : blocks) dfree(c, g);
+        return cuda_fail(e);
+    }
+    free_all();
+    nb = FA;
+    return GJ_OK;
 }
 
 }  // namespace
@@ -316,90 +644,26 @@ gj_status cyc_summarize(QueryState &q, uint64_t *total_out) {
     } while (0)
     std::vector<uint32_t *> cur(1, nullptr);   // the current items' groups, by relation
     {
-        // items of relation 0: all its groups
-        int64_t F = q.r[0].F->G;
-        TRY(dalloc(c, &cur[0], F));
-        if (F > 0) { k_cyc_iota<<<grid_of(c, F), CT, 0, c.stream>>>(cur[0], F); c.launches++; }
-        TRY(cudaGetLastError());
-        for (int j = 1; j < k && e == cudaSuccess; j++) {
-            const QRel &t = q.r[j];
-            StepSpec s{};
-            s.j = j;
-            s.nshared = (int)t.sep_cols.size();
-            for (int ci = 0; ci < s.nshared; ci++) {
-                const QRel &h = q.r[t.cyc_src_rel[ci]];
-                s.src_key[ci] = h.F->gkey + (int64_t)t.cyc_src_col[ci] * h.F->G;
-                s.src_pos[ci] = t.cyc_src_rel[ci];
-                s.dst_key[ci] = t.F->gkey + (int64_t)t.sep_cols[ci] * t.F->G;
-            }
-            s.G = t.F->G;
-            for (int p = 0; p < j; p++) s.item_grp[p] = cur[p];
-            s.err = c.err;
-            Temps tmp(c);
-            uint64_t *cnt = nullptr, *excl = nullptr, *tot = nullptr;
-            uint32_t *lo = nullptr;
-            TRY(tmp.alloc(&cnt, F));
-            TRY(tmp.alloc(&excl, F));
-            TRY(tmp.alloc(&lo, F));
-            TRY(tmp.alloc(&tot, 1));
-            // a table over the value ranges of relation j's first one or
-            // two shared columns, when it stays small (at most 2^24 entries)
-            {
-                constexpr int64_t MAX_RANGE = 1ll << 24;
-                int64_t nv[2] = {0, 0};
-                for (int ci = 0; ci < std::min(2, s.nshared); ci++) {
-                    const int col = t.sep_cols[ci];
-                    nv[ci] = (int64_t)t.R->kmax[col] - (int64_t)t.R->kmin[col] + 1;
-                }
-                int rc = std::min(2, s.nshared);
-                if (rc == 2 && nv[0] * nv[1] > MAX_RANGE) rc = 1;
-                if (rc == 1 && nv[0] > MAX_RANGE) rc = 0;
-                if (t.F->G > 0 && rc > 0) {
-                    const int64_t nx = rc == 2 ? nv[0] * nv[1] : nv[0];
-                    s.range_cols = rc;
-                    for (int ci = 0; ci < rc; ci++) {
-                        s.range_mn[ci] = t.R->kmin[t.sep_cols[ci]];
-                        s.range_nv[ci] = (uint32_t)nv[ci];
-                    }
-                    uint32_t *rl = nullptr;
-                    TRY(tmp.alloc(&rl, nx + 1));
-                    k_cyc_ranges<<<grid_of(c, nx + 1), CT, 0, c.stream>>>(s, nx, rl); c.launches++;
-                    TRY(cudaGetLastError());
-                    s.range_lo = rl;
-                }
-            }
-            uint64_t Fout = 0;
-            if (F > 0) {
-                k_cyc_count<<<grid_of(c, F), CT, 0, c.stream>>>(s, F, cnt, lo); c.launches++;
-                TRY(cudaGetLastError());
-                TRY(scan_u64_sat(c, cnt, nullptr, excl, F, tot, nullptr, nullptr));
-                TRY(read_u64(c, tot, &Fout));
-            }
-            if (Fout > 0x7fffffffull) {   // more partial blocks than this path holds
-                for (auto &g : cur) dfree(c, g);
-                return GJ_ERR_OOM;
-            }
-            std::vector<uint32_t *> nxt(j + 1, nullptr);
-            bool ok = true;
-            for (int p = 0; p <= j && ok; p++) ok = dalloc(c, &nxt[p], (int64_t)Fout) == cudaSuccess;
-            if (!ok) {
-                for (auto &g : nxt) dfree(c, g);
-                for (auto &g : cur) dfree(c, g);
-                return GJ_ERR_OOM;
-            }
-            if (Fout > 0) {
-                OutGrp og{};
-                for (int p = 0; p <= j; p++) og.g[p] = nxt[p];
-                uint32_t *tf = nullptr;
-                const int64_t tiles = ((int64_t)Fout + WT - 1) / WT;
-                TRY(tmp.alloc(&tf, tiles));
-                k_cyc_tile_first<<<grid_of(c, F), CT, 0, c.stream>>>(F, cnt, excl, tf); c.launches++;
-                k_cyc_write<<<grid_of(c, (int64_t)Fout), CT, 0, c.stream>>>(s, F, excl, lo, (int64_t)Fout, tf, og); c.launches++;
-            }
-            for (auto &g : cur) dfree(c, g);
-            cur = nxt;
-            F = (int64_t)Fout;
+        int64_t F = 0;
+        bool split = false;
+        gj_status sst = cyc_split(q, cur, F, split);
+        if (sst != GJ_OK) return sst;
+        if (!split) {
+            // one clique: items of relation 0 (all its groups), then every
+            // relation in query order
+            F = q.r[0].F->G;
+            TRY(dalloc(c, &cur[0], F));
+            if (F > 0) { k_cyc_iota<<<grid_of(c, F), CT, 0, c.stream>>>(cur[0], F); c.launches++; }
             TRY(cudaGetLastError());
+            for (int j = 1; j < k; j++) {
+                RangeInfo ri;
+                StepSpec s = relation_step(q, j, ri);
+                gj_status st = cyc_step(c, s, ri, cur, F);
+                if (st != GJ_OK) {
+                    for (auto &g : cur) dfree(c, g);
+                    return st;
+                }
+            }
         }
         // blocks: their sizes, first rows and |Q|
         q.cyc_grp = cur;
