@@ -83,8 +83,9 @@ def workload_name(a):
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "square":
         return ("square: cyclic R0(A,B) R1(B,C) R2(C,D) R3(D,A), 10^5 rows/table, int32 keys "
-                "uniform over [0,1000), int64 payload/table, one maxclique {A,B,C,D} joined "
-                f"group-wise relation by relation, desummarised in 2^{a.chunk_log2}-row chunks")
+                "uniform over [0,1000), int64 payload/table, junction tree of two maxcliques "
+                "{A,B,C} and {C,D,A} joined on {A,C}, "
+                f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "star_poisson":
         return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
                 "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "

@@ -1,10 +1,11 @@
 // gj_cyclic.cu -- cyclic queries in general (Sections 3.2.1 and 3.4).
 //
 // A query whose relation order gives no join tree is answered over a
-// junction tree.  Here it is the junction tree of one maxclique holding
-// every attribute: its potential (Algorithm 1: the relations' potentials
-// joined, frequencies multiplied) is built at the level of groups (distinct
-// key tuples), relation by relation in query order:
+// junction tree: two maxcliques where the second can be built as below
+// (cyc_split), else one maxclique holding every attribute.  A clique's
+// potential (Algorithm 1: the relations' potentials joined, frequencies
+// multiplied) is built at the level of groups (distinct key tuples),
+// relation by relation in query order:
 //
 //   items_0 = every group of relation 0
 //   items_j = { (g_0..g_j-1, g) : g a group of relation j whose values of
@@ -13,7 +14,8 @@
 //
 // Relation j's factor is ordered by those shared columns first, so the
 // matching groups of an item are one contiguous range, found by two binary
-// searches; inside it the groups follow j's new attributes in V order.  So
+// searches (or read off a table over the shared values); inside it the
+// groups follow j's new attributes in V order.  So
 // the final items (the blocks: one group per relation, consistent on every
 // shared attribute) come out in V order with no sort, V being the
 // attributes in order of first appearance.  A block stands for the

@@ -118,3 +118,16 @@ def test_key_ranges_wide_narrow_and_negative(ctx, spread):
     for R in q.relations:
         R.keys[:] = [(k.astype(np.int64) * spread - (5 if spread < 0 else 0)).astype(np.int32) for k in R.keys]
     assert cyclic_parity(ctx, q, windows=[(5, 999)]) > 0
+
+
+@pytest.mark.parametrize("flip", [False, True])
+def test_two_cliques_and_one(ctx, flip):
+    """A 4-cycle with R3 declared (D, A) is answered on two maxcliques
+    ({A,B,C} and {C,D,A}, joined on {A,C}); declared (A, D) its join inside
+    the second clique is not on a leading column, and it stays on one
+    maxclique.  The rows are the oracle's either way."""
+    q = G.cyclic_query(8400, "square", [700, 650, 600, 550], domain=40, s=0.7)
+    if flip:
+        R = q.relations[3]
+        q.relations[3] = G.Relation(R.name, R.attrs[::-1], R.keys[::-1], R.payloads)
+    assert cyclic_parity(ctx, q, windows=[(0, 4097), (12345, 777)]) > 4096
