@@ -216,24 +216,31 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
 /*
  * Plans a query over relations rel_ids[0..n_rel-1] (rel_ids[0] is the root).
  * Relation j > 0 hangs under the first earlier relation that holds every
- * attribute j shares with relations 0..j-1; if there is none the order does
- * not give a join tree (GJ_ERR_NOT_ACYCLIC); if j shares nothing the query
- * is rejected (GJ_ERR_INVALID).  The result's key columns V are a preorder
+ * attribute j shares with relations 0..j-1; if j shares nothing the query
+ * is rejected (GJ_ERR_INVALID); if no earlier relation holds them all the
+ * order gives no join tree and the query is cyclic (below).  The result's key columns V are a preorder
  * walk of that tree, every relation adding the attributes its parent lacks
  * in declared column order; payload columns follow, relation by relation.
  * Rows of the result are ordered by V (signed int32, ascending), ties broken
  * by the original row ids r_1..r_k (Def. 1 sorts the result by all columns).
  * Builds any factor it needs.
  *
- * One cyclic shape is accepted as well: three relations of two key columns
- * each, every pair sharing exactly one attribute (R0(A,B), R1(B,C), R2(C,A)
- * in any column order).  Its junction tree has the single maxclique
- * {A,B,C}, whose joint potential (Section 3.2.1, Algorithm 1: the join of
- * the three factors, frequencies multiplied) is the summary: the triples of
- * groups that close the cycle.  V
- * is R0's columns in declared order, then C; rows are ordered as above.
+ * Cyclic queries (Sections 3.2.1, 3.4; 2 to 8 relations, every relation
+ * after the first sharing an attribute with those before it) are answered
+ * over a junction tree: the summary is the joint potential of its
+ * maxcliques (Algorithm 1: the factors joined, frequencies multiplied), as
+ * blocks of one group per relation.  The 3-cycle R0(A,B) R1(B,C) R2(C,A)
+ * (two key columns each, any column order) uses the maxclique {A,B,C};
+ * other shapes use two maxcliques (relations 0-1 and the rest, joined on
+ * their common attributes) where the second clique's relations join one
+ * another on the leading columns of their factors, else one maxclique
+ * holding every attribute.  V is the attributes in order of first
+ * appearance (relation 0's columns in declared order, then each relation's
+ * new attributes in declared order); rows are ordered as above.  Queries
+ * whose intermediate blocks would exceed 2^31 return GJ_ERR_OOM.
  * gj_summarize and gj_desummarize work as for a tree; gj_level,
- * gj_summary_groups and gj_summary_save return GJ_ERR_INVALID for it.
+ * gj_summary_groups, gj_summary_save and the row-sharded counting calls
+ * return GJ_ERR_INVALID for them.
  */
 gj_status gj_query_create(gj_ctx *ctx, const int32_t *rel_ids, int32_t n_rel, gj_query **out);
 
