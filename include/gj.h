@@ -232,9 +232,10 @@ gj_status gj_factor_export(gj_ctx *ctx, int32_t rel_id, const int32_t *col_order
  * blocks of one group per relation.  The 3-cycle R0(A,B) R1(B,C) R2(C,A)
  * (two key columns each, any column order) uses the maxclique {A,B,C};
  * other shapes use two maxcliques (relations 0-1 and the rest, joined on
- * their common attributes) where the second clique's relations join one
- * another on the leading columns of their factors, else one maxclique
- * holding every attribute.  V is the attributes in order of first
+ * their common attributes) where every relation of the second clique after
+ * its first shares an attribute with the ones before it and the second
+ * clique's attributes pack into 64 bits, else one maxclique holding every
+ * attribute.  V is the attributes in order of first
  * appearance (relation 0's columns in declared order, then each relation's
  * new attributes in declared order); rows are ordered as above.  Queries
  * whose intermediate blocks would exceed 2^31 return GJ_ERR_OOM.

@@ -381,10 +381,10 @@ StepSpec relation_step(QueryState &q, int j, RangeInfo &ri) {
 // (every 3-path of a 4-cycle) never appear.  The blocks come out in V order:
 // clique 1's items in V order, each one's matches in the order of clique
 // 2's other attributes.  Taken when every relation of clique 2 after the
-// first joins the earlier ones of its clique on a leading run of its
-// shared columns (its factor is ordered by those first), S is not empty,
-// and clique 2's attributes pack into one 64-bit word; otherwise the query
-// stays on one clique (applied = false).
+// first shares an attribute with the earlier ones of its clique (plan_cyclic
+// orders its factor by those columns first), S is not empty, and clique 2's
+// attributes pack into one 64-bit word; otherwise the query stays on one
+// clique (applied = false).
 gj_status cyc_split(QueryState &q, std::vector<uint32_t *> &blocks, int64_t &nb, bool &applied) {
     applied = false;
     const int k = q.k;
@@ -576,7 +576,8 @@ void cyc_free(Ctx &c, QueryState &q) {
 
 // The plan of a cyclic query (no join tree in this relation order): each
 // relation after the first must share an attribute with those before it.
-// Factor orders: shared columns first (declared order), then the others;
+// Factor orders: shared columns first (declared order; from relation 3 on,
+// those shared with relations 2..j-1 ahead of the others), then the rest;
 // V by first appearance.  False if the query is not of that form.
 bool plan_cyclic(QueryState &q) {
     const int k = q.k;
@@ -608,6 +609,29 @@ bool plan_cyclic(QueryState &q) {
             }
         }
         if (j > 0 && t.sep_cols.empty()) return false;   // a cross product
+        if (j >= 3 && k >= 4) {
+            // shared columns whose attribute relations 2..j-1 hold come
+            // first (stable): the factor is then ordered so that the second
+            // clique of cyc_split can join relation j on a leading run
+            auto in_second = [&](int c) {
+                for (int i = 2; i < j; i++)
+                    for (int cc = 0; cc < q.r[i].R->nk; cc++)
+                        if (q.r[i].R->attr[cc] == t.R->attr[c]) return true;
+                return false;
+            };
+            std::vector<int> order(t.sep_cols.size());
+            for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+            std::stable_partition(order.begin(), order.end(), [&](int i) { return in_second(t.sep_cols[i]); });
+            std::vector<int> sc, sr, sl;
+            for (int i : order) {
+                sc.push_back(t.sep_cols[i]);
+                sr.push_back(t.cyc_src_rel[i]);
+                sl.push_back(t.cyc_src_col[i]);
+            }
+            t.sep_cols = sc;
+            t.cyc_src_rel = sr;
+            t.cyc_src_col = sl;
+        }
         if (j > 0) t.parent = t.cyc_src_rel[0];            // reported by gj_query_sizes
         for (int c = 0; c < t.R->nk; c++)
             if (find(t.R->attr[c]) < 0) {

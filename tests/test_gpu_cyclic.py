@@ -122,10 +122,10 @@ def test_key_ranges_wide_narrow_and_negative(ctx, spread):
 
 @pytest.mark.parametrize("flip", [False, True])
 def test_two_cliques_and_one(ctx, flip):
-    """A 4-cycle with R3 declared (D, A) is answered on two maxcliques
-    ({A,B,C} and {C,D,A}, joined on {A,C}); declared (A, D) its join inside
-    the second clique is not on a leading column, and it stays on one
-    maxclique.  The rows are the oracle's either way."""
+    """A 4-cycle is answered on two maxcliques ({A,B,C} and {C,D,A}, joined
+    on {A,C}) whichever way its last relation's columns are declared (its
+    factor is ordered by D, the column it shares with R2, first); the rows
+    are the oracle's either way."""
     q = G.cyclic_query(8400, "square", [700, 650, 600, 550], domain=40, s=0.7)
     if flip:
         R = q.relations[3]
