@@ -83,8 +83,7 @@ def workload_name(a):
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "square":
         return ("square: cyclic R0(A,B) R1(B,C) R2(C,D) R3(D,A), 10^5 rows/table, int32 keys "
-                "uniform over [0,1000), int64 payload/table, junction tree of two maxcliques "
-                "{A,B,C} and {C,D,A} joined on {A,C}, "
+                "uniform over [0,1000), int64 payload/table, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "star_poisson":
         return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
