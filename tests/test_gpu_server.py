@@ -152,3 +152,38 @@ def test_slot_arena_option_range():
             ctx.set_option(gj.GJ_OPT_SLOT_ARENA, bad)
         assert e.value.status == gj.GJ_ERR_INVALID
     ctx.close()
+
+
+def test_server_answers_cyclic_queries():
+    """Cyclic queries (a 3-cycle, a 4-cycle on two maxcliques, two triangles
+    sharing an edge) served beside trees, with a small slot arena so that
+    their intermediate items spill into the pools: sizes and streamed rows
+    equal the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10435_gb300 import gj
+    ctx = gj.Context(0, torch.cuda.Stream())
+    ctx.set_option(gj.GJ_OPT_SLOT_ARENA, 1 << 20)
+    pool = [G.triangle_query(51, [300, 280, 260], domain=25),
+            G.cyclic_query(52, "square", [400, 380, 360, 340], domain=30),
+            G.cyclic_query(53, "diamond", 150, domain=12)] + _small_pool(n=3, seed=23)
+    ref = [O.count(q).total for q in pool]
+    ids = [gj.load_query(ctx, q) for q in pool]
+    chunk = 1 << 12
+    limit = 2 * chunk + 3
+    srv = gj.NativeServer(ctx, n_slots=3, chunk_rows=chunk, max_rows=limit)
+    picks = [i % len(ids) for i in range(24)]
+    res, _ = srv.run([ids[p] for p in picks], np.zeros(len(picks)))
+    srv.close()
+    hashes = {}
+    for qi, q in enumerate(pool):
+        j = O.join(q)
+        hashes[qi] = _hash_columns(O.columns(q, j.rowids[:min(limit, ref[qi])]))
+    for r, p in zip(res, picks):
+        assert r["status"] == gj.GJ_OK
+        assert r["total"] == ref[p] and r["rows"] == min(limit, ref[p])
+        assert r["hash"] == hashes[p]
+    for q in ids:
+        for x in q:
+            ctx.release_relation(x)
+    ctx.close()
