@@ -267,7 +267,7 @@ __device__ __forceinline__ bool sep_head(const KeyCols &sep, int64_t g) {
 // NCH >= 0: exactly NCH children; NCH < 0: s.nch.  SEP1: the separator is
 // one column (heads found from a staged copy of it), else any number.
 template <int NCH, bool SEP1>
-__global__ void __launch_bounds__(ST)
+__global__ void __launch_bounds__(ST, NCH >= 3 ? 3 : 1)
 k_up_scan(UpSpec s) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *s_w = (uint64_t *)smem;                 // the element's w
@@ -575,7 +575,7 @@ template <int NCH>
 __global__ void __launch_bounds__(ST)
 k_down(DownSpec s) {
     constexpr int CAP = NCH >= 0 ? (NCH > 0 ? NCH : 1) : MAX_REL;
-    constexpr int IT = NCH >= 0 ? DN_ITEMS : 1;
+    constexpr int IT = NCH >= 3 ? DN_ITEMS / 2 : NCH >= 0 ? DN_ITEMS : 1;   // fewer registers with many children
     const int nch = NCH >= 0 ? NCH : s.nch;
     __shared__ AggTable tab;
     __shared__ uint32_t s_use[CAP], s_hits[CAP];
