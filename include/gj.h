@@ -481,16 +481,18 @@ gj_status gj_shard_down(gj_query *q, int32_t rel, const uint64_t *down_in, int32
  * *n_groups.  key_cols is a host array of n_keys device pointers.  Work is
  * enqueued on `cuda_stream` on `device`.  Every call waits for that stream
  * before it returns: it reads the key ranges, the group count and the
- * device error word back into host memory.
+ * device error word back into host memory.  So no call can be captured
+ * into a CUDA graph: on a capturing stream the synchronisation fails and
+ * invalidates the capture.
  *
  * All scratch lives in one fixed device array inside the library (about
  * 6.7 MB, held on every device that loads the library until the process
  * exits), so n_rows may not exceed GJ_NOALLOC_MAX_ROWS: larger inputs return
  * GJ_ERR_INVALID before any work is enqueued.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call shares the array and
- * keeps its last contents: calls whose work overlaps on the GPU (other
- * streams, other threads) race and must be serialised by the caller.
+ * looks up that array's device address (cudaGetSymbolAddress).  Every call
+ * shares the array and keeps its last contents: calls whose work overlaps on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.
  */
 #define GJ_NOALLOC_MAX_ROWS (1 << 18)
 gj_status gj_factor_build_noalloc(int32_t device, void *cuda_stream, int64_t n_rows,
