@@ -55,6 +55,7 @@ def parse():
                         "(0: the whole result)")
     p.add_argument("--queries", type=int, default=4096, help="batch workload: queries")
     p.add_argument("--rows", type=int, default=10**7)
+    p.add_argument("--fact-rows", type=int, default=10**8, help="star_poisson workload: fact rows")
     p.add_argument("--domain", type=int, default=10**6)
     p.add_argument("--zipf", type=float, default=1.1)
     p.add_argument("--drop-attrs", default="",
@@ -86,7 +87,7 @@ def workload_name(a):
                 "uniform over [0,1000), int64 payload/table, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     if a.workload == "star_poisson":
-        return ("star_poisson: fact F(K1..K4,P) 10^8 rows, K_j uniform over [0,10^6), joined to "
+        return (f"star_poisson: fact F(K1..K4,P) {a.fact_rows} rows, K_j uniform over [0,10^6), joined to "
                 "4 dimensions D_j(K_j,P_j) with Poisson(2) copies of every key, int64 payloads, "
                 f"desummarised in 2^{a.chunk_log2}-row chunks")
     return (f"chain5_zipf: 5-table chain R_i(K_i-1,K_i), {a.rows} rows/table, int32 keys "
@@ -108,7 +109,7 @@ def make_query(a, rank):
     if a.workload == "chain3_uniform":
         return G.chain3_uniform(seed=G.SEED_BASE + 0 + 1000 * rank)
     if a.workload == "star_poisson":
-        return G.star_poisson(seed=G.SEED_BASE + 2 + 1000 * rank)
+        return G.star_poisson(seed=G.SEED_BASE + 2 + 1000 * rank, fact_rows=a.fact_rows)
     if a.workload == "triangle":
         return G.triangle_query(G.SEED_BASE + 5 + 1000 * rank, [10**6] * 3, domain=1000)
     if a.workload == "square":
