@@ -234,7 +234,10 @@ class NumpyShard:
 
 def _sharded_query(seed):
     from paper_2206_10435_gb300 import datagen as G
-    # a chain and a star-shaped tree (a relation with two children)
+    # a chain and a star-shaped tree (a relation with two children); seed 0:
+    # two rows per relation, so a third rank holds no rows at all
+    if seed == 0:
+        return G.chain3_uniform(seed=11, rows=2, end_domain=2, mid_domain=1)
     if seed % 2:
         return G.chain3_uniform(seed=seed, rows=400, end_domain=60, mid_domain=12)
     q = G.chain3_uniform(seed=seed, rows=300, end_domain=40, mid_domain=10)
@@ -255,16 +258,18 @@ def _rank_sharded(rank, world, port, out, seed):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("seed", [3, 4])
-def test_two_gloo_ranks_row_sharded_counting_matches_the_oracle(seed):
-    """Every relation split by rows over two ranks: the total and every key
-    tuple's multiplicity (summed over the ranks' local groups) equal the
-    oracle's counting pass on the whole relations."""
+@pytest.mark.parametrize("world,seed", [(2, 3), (2, 4), (3, 3), (3, 4), (3, 0)])
+def test_gloo_ranks_row_sharded_counting_matches_the_oracle(world, seed):
+    """Every relation split by rows over two or three ranks (rows not a
+    multiple of the rank count; with seed 0 one rank holds no rows): the total
+    and every key tuple's multiplicity (summed over the ranks' local groups)
+    equal the oracle's counting pass on the whole relations."""
     from oracle import oracle as O
-    res = _spawn(_rank_sharded, 2, seed)
+    res = _spawn(_rank_sharded, world, seed)
     q = _sharded_query(seed)
     c = O.count(q, rows=True)
-    assert res[0][1] == res[1][1] == int(c.total) > 0
+    assert len(res) == world
+    assert all(r[1] == int(c.total) for r in res) and int(c.total) > 0
     want = O.group_mult_from_counts(q, c)
     for t, (allk, m) in enumerate(want):
         got = {}
