@@ -266,6 +266,32 @@ def random_tree_query(seed: int, n_rel: int, max_rows: int = 6, domain: int = 3,
     return Query(f"tree{seed}", rels, {a: f"X{a}" for a in range(next_attr)})
 
 
+_INT32_ENDS = np.array([-2**31, -2**31 + 1, -1, 0, 2**31 - 2, 2**31 - 1], dtype=np.int64)
+
+
+def extreme_keys(q: Query, seed: int) -> Query:
+    """The same query with every attribute's values mapped one-to-one, by a
+    seeded permutation per attribute, onto values at both ends of the int32
+    range and around zero (INT32_MIN, INT32_MIN + 1, -1, 0, INT32_MAX - 1,
+    INT32_MAX).  Which rows join is unchanged; the sorted order of the result
+    is not.  The input's key values must lie in [-1, 4] (random_tree_query
+    with domain <= 5)."""
+    rng = np.random.default_rng(seed)
+    maps = {}
+    rels = []
+    for R in q.relations:
+        cols = []
+        for a, k in zip(R.attrs, R.keys):
+            if a not in maps:
+                maps[a] = rng.permutation(_INT32_ENDS)
+            idx = k.astype(np.int64) + 1
+            if idx.size and (idx.min() < 0 or idx.max() >= _INT32_ENDS.shape[0]):
+                raise ValueError("key values outside [-1, 4]")
+            cols.append(maps[a][idx].astype(np.int32))
+        rels.append(Relation(R.name, list(R.attrs), cols, list(R.payloads)))
+    return Query(q.name + "_ends", rels, dict(q.attr_names))
+
+
 def batch_queries_torch(seed: int = SEED_BASE + 3, n_queries: int = 4096,
                         min_tables: int = 3, max_tables: int = 6,
                         rows_range=(10**3, 10**6), domain_range=(10**2, 10**5),

@@ -387,6 +387,18 @@ def test_larger_random_trees_with_multi_attribute_separators(ctx, seed):
     full_parity(ctx, q, windows=[(0, 1000), (1001, 1025)])
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_keys_at_the_int32_ends(ctx, seed):
+    # every key value at INT32_MIN, INT32_MIN + 1, -1, 0, INT32_MAX - 1 or
+    # INT32_MAX: key ranges span 2^32 - 1, sort words and links must not wrap,
+    # and the result follows the signed order
+    base = G.random_tree_query(2300 + seed, 2 + seed % 4, max_rows=60, domain=5, max_new=2,
+                               min_rows=20, max_shared=1 + seed % 2)
+    q = G.extreme_keys(base, seed)
+    assert O.count(q).total == O.count(base).total
+    full_parity(ctx, q, windows=[(0, 1), (3, 700)])
+
+
 @pytest.mark.parametrize("hops", [3, 4])
 def test_sensitivity_variants(ctx, hops):
     # Section 4.2: the duplicated form multiplies |Q| by 2^k; the extra hop

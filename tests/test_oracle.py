@@ -567,6 +567,36 @@ def test_oracle_matches_nested_loops_multi_attribute_separators(q):
         assert [tuple(t) for t in O.join(q).rowids.tolist()] == [tuple(t) for t in bf]
 
 
+def _int32_end_queries():
+    qs = []
+    for seed in range(30):
+        n_rel = 1 + seed % 4
+        base = G.random_tree_query(2100 + seed, n_rel, max_rows=5 if n_rel <= 2 else 4,
+                                   domain=3, max_new=2, min_rows=1, max_shared=2)
+        qs.append(G.extreme_keys(base, seed))
+    return qs
+
+
+@pytest.mark.parametrize("q", _int32_end_queries(), ids=lambda q: q.name)
+def test_oracle_matches_nested_loops_at_the_int32_ends(q):
+    # keys at INT32_MIN, INT32_MAX and around zero: the result is ordered by
+    # the signed values (no wrap in a key difference or a packed word) and
+    # the levels' runs follow that order
+    pl = O.plan(q)
+    bf = canonical(q, brute_force(q), pl.V)
+    c = O.count(q, rows=True)
+    assert c.total == len(bf)
+    if not bf:
+        return
+    j = O.join(q)
+    assert [tuple(t) for t in j.rowids.tolist()] == [tuple(t) for t in bf]
+    lv = O.gfjs_levels(q, j.rowids)
+    ref = levels_by_definition(q, bf, pl.V)
+    for l in range(len(pl.V)):
+        assert [list(x) for x in zip(lv[l].value.tolist(), lv[l].freq.tolist(),
+                                     lv[l].offset.tolist())] == ref[l]
+
+
 def test_duplicated_tables_multiply_the_join_size():
     base = G.chain_sensitivity(rows=2000, domain=500, hops=3)
     assert O.count(G.duplicate_rows(base)).total == 8 * O.count(base).total
