@@ -307,7 +307,8 @@ gj_status gj_summary_groups(gj_query *q, int32_t rel, uint64_t *w_dev, uint64_t 
  * (Algorithm 4 emits one entry per prefix), restricted to runs that START
  * in result rows [row0, row0 + n_rows).  Writes value (int32), freq and
  * offset (uint64) of each run into device arrays of capacity `cap`; *n_out
- * receives the number of runs (GJ_ERR_CAPACITY if above cap).
+ * receives the number of runs (GJ_ERR_CAPACITY if above cap).  Window rules
+ * as for gj_desummarize; a level outside 0..n_vars-1 is GJ_ERR_INVALID.
  */
 gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
                    int32_t *value_dev, uint64_t *freq_dev, uint64_t *offset_dev,
@@ -326,7 +327,11 @@ gj_status gj_level(gj_query *q, int32_t level, uint64_t row0, uint64_t n_rows,
  * staging buffer or a copy.  Pageable host memory is rejected
  * (GJ_ERR_INVALID).  *n_out receives the number of rows written; the rows
  * are in place once the context's stream reaches this point (the call
- * synchronises it).  Requires gj_summarize.
+ * synchronises it).  Requires gj_summarize (else GJ_ERR_STATE; after an
+ * overflow, GJ_ERR_OVERFLOW).  A window of no rows, or starting at or past
+ * |Q|, writes nothing (*n_out = 0); one that reaches past |Q| is clipped
+ * (n_rows may be up to UINT64_MAX); a clipped window of more than
+ * 2^31 - 1 rows is GJ_ERR_INVALID, refused before anything is written.
  */
 gj_status gj_desummarize(gj_query *q, uint64_t row0, uint64_t n_rows,
                          void *const *out_cols, uint32_t *const *rowid_cols, uint64_t *n_out);

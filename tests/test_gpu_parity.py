@@ -399,6 +399,62 @@ def test_keys_at_the_int32_ends(ctx, seed):
     full_parity(ctx, q, windows=[(0, 1), (3, 700)])
 
 
+def test_window_contract(ctx):
+    """Windows of gj_desummarize and gj_level: GJ_ERR_STATE before the
+    summary; empty windows and windows at or past |Q| write nothing; a
+    window reaching past |Q| is clipped (n_rows up to 2^64 - 1); a level
+    index out of range is invalid; too small a capacity reports
+    GJ_ERR_CAPACITY; a clipped window of 2^31 rows or more is invalid."""
+    from paper_2206_10435_gb300 import gj
+    q = G.chain3_uniform(seed=5, rows=300, end_domain=30, mid_domain=6)
+    run = Run(ctx, q)
+    for call in (lambda: run.q.desummarize(0, 4), lambda: run.q.level(0, 0, 4, cap=4)):
+        with pytest.raises(gj.GJError) as e:
+            call()
+        assert e.value.status == gj.GJ_ERR_STATE
+    total = run.summarize()
+    assert total == O.count(q).total > 3
+    j = O.join(q)
+    ref = O.columns(q, j.rowids)
+    for r0, n in [(0, 0), (total, 5), (total + 1000, 5), (1 << 63, 5)]:
+        assert all(c.numel() == 0 for c in run.q.desummarize(r0, n))
+        assert run.q.level(0, r0, n, cap=4)[0].numel() == 0
+    cols = run.q.desummarize(total - 3, (1 << 64) - 1, out=run.q.alloc_columns(3))
+    assert cols[0].shape[0] == 3
+    for a, b in zip(cols, ref):
+        assert np.array_equal(a.cpu().numpy(), b[total - 3:])
+    lv = O.gfjs_levels(q, j.rowids)
+    with pytest.raises(gj.GJError) as e:
+        run.q.level(len(lv), 0, total)
+    assert e.value.status == gj.GJ_ERR_INVALID
+    k = lv[0].value.shape[0]
+    assert k > 1
+    with pytest.raises(gj.GJError) as e:
+        run.q.level(0, 0, total, cap=k - 1)
+    assert e.value.status == gj.GJ_ERR_CAPACITY
+    assert np.array_equal(run.q.level(0, 0, total, cap=k)[0].cpu().numpy(), lv[0].value)
+    run.close()
+    # all keys equal: |Q| = 2000^3 > 2^31, so a window of 2^31 rows is refused
+    # before anything is written
+    big = G.Query("equal3", [G.Relation(f"R{i}", [i, i + 1], [np.full(2000, 7, np.int32)] * 2, [])
+                             for i in range(3)], {a: f"X{a}" for a in range(4)})
+    run = Run(ctx, big)
+    assert run.summarize() == 2000 ** 3 == O.count(big).total
+    for call in (lambda: run.q.desummarize(5, 1 << 31, out=run.q.alloc_columns(1)),
+                 lambda: run.q.level(2, 0, 1 << 31, cap=1)):
+        with pytest.raises(gj.GJError) as e:
+            call()
+        assert e.value.status == gj.GJ_ERR_INVALID
+    # rows past 2^32 (64-bit digit arithmetic): all keys equal, so row r is
+    # the row-id tuple (r // 2000^2, r // 2000 % 2000, r % 2000)
+    r0 = (1 << 32) + 5
+    cols, rids = run.q.desummarize(r0, 2, out=run.q.alloc_columns(2), rowids=True)
+    assert [c.cpu().tolist() for c in cols] == [[7, 7]] * 4
+    for i, r in enumerate((r0, r0 + 1)):
+        assert [int(t[i]) for t in rids] == [r // 2000 ** 2, r // 2000 % 2000, r % 2000]
+    run.close()
+
+
 @pytest.mark.parametrize("hops", [3, 4])
 def test_sensitivity_variants(ctx, hops):
     # Section 4.2: the duplicated form multiplies |Q| by 2^k; the extra hop
