@@ -97,6 +97,49 @@ def test_overflow_reported(ctx):
     run.close()
 
 
+@pytest.mark.parametrize("shape", ["triangle", "square"])
+def test_window_contract(ctx, shape):
+    """The desummarise windows of the two cyclic paths (the 3-cycle's and
+    the junction tree's): GJ_ERR_STATE before the summary, empty windows and
+    windows at or past |Q| write nothing, a window reaching past |Q| is
+    clipped, a clipped window of 2^31 rows is refused, and rows past 2^32 of
+    one huge block (all keys equal: n^k rows, row r the row-id tuple of r's
+    base-n digits) are exact."""
+    from paper_2206_10435_gb300 import gj
+    tri = shape == "triangle"
+    attrs = [(0, 1), (1, 2), (2, 0)] if tri else G.CYCLIC_SHAPES["square"]
+    q = G.triangle_query(77, [300, 250, 200], domain=20) if tri else \
+        G.cyclic_query(31, "square", 120, domain=10)
+    run = Run(ctx, q)
+    with pytest.raises(gj.GJError) as e:
+        run.q.desummarize(0, 4)
+    assert e.value.status == gj.GJ_ERR_STATE
+    total = run.summarize()
+    assert total == O.count(q).total > 3
+    j = O.join(q)
+    ref = O.columns(q, j.rowids)
+    for r0, n in [(0, 0), (total, 5), (1 << 63, 5)]:
+        assert all(c.numel() == 0 for c in run.q.desummarize(r0, n))
+    cols = run.q.desummarize(total - 3, (1 << 64) - 1, out=run.q.alloc_columns(3))
+    for a, b in zip(cols, ref):
+        assert np.array_equal(a.cpu().numpy(), b[total - 3:])
+    run.close()
+    n, k = (2000, 3) if tri else (300, 4)
+    eq = G.Query(shape + "_equal", [G.Relation(f"R{i}", list(at), [np.full(n, 7, np.int32) for _ in at])
+                                    for i, at in enumerate(attrs)])
+    run = Run(ctx, eq)
+    assert run.summarize() == n ** k
+    with pytest.raises(gj.GJError) as e:
+        run.q.desummarize(5, 1 << 31, out=run.q.alloc_columns(1))
+    assert e.value.status == gj.GJ_ERR_INVALID
+    r0 = (1 << 32) + 5
+    cols, rids = run.q.desummarize(r0, 2, out=run.q.alloc_columns(2), rowids=True)
+    assert [c.cpu().tolist() for c in cols] == [[7, 7]] * len(cols)
+    for i, r in enumerate((r0, r0 + 1)):
+        assert [int(t[i]) for t in rids] == [r // n ** (k - 1 - p) % n for p in range(k)]
+    run.close()
+
+
 def test_tree_only_calls_rejected(ctx):
     from paper_2206_10435_gb300 import gj
     run = Run(ctx, G.cyclic_query(9, "square", 30, domain=4))
