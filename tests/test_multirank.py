@@ -106,6 +106,41 @@ def test_two_gloo_ranks_gather_and_exact_saturating_sum():
         assert m == 4.0
 
 
+def _batch_list():
+    from paper_2206_10435_gb300 import datagen as G
+    return G.batch_queries(seed=41, n_queries=7, rows_range=(50, 2000), domain_range=(10, 200))
+
+
+def _rank_batch(rank, world, port, out):
+    dist = _init(rank, world, port)
+    from oracle import oracle as O
+    from paper_2206_10435_gb300 import partition as P
+    qs = _batch_list()
+    lo, hi = P.query_block(len(qs), rank, world)
+    # this rank's block of the global list, counted (the oracle stands in
+    # for the GPU path; the split and the gather are what is tested)
+    local = np.array([min(int(O.count(q).total), SAT) for q in qs[lo:hi]], dtype=np.uint64)
+    gathered = P.gather_in_order(dist, local, len(qs), rank, world)
+    out.put((rank, (lo, hi), [int(x) for x in gathered]))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_gloo_ranks_split_a_query_list_and_gather_totals_in_order(world):
+    """A list of 7 chain queries split into contiguous blocks over two or
+    three ranks: the blocks cover the list once, and every rank gets every
+    query's total, in query order."""
+    from oracle import oracle as O
+    res = _spawn(_rank_batch, world)
+    want = [min(int(O.count(q).total), SAT) for q in _batch_list()]
+    assert any(w > 0 for w in want)
+    blocks = [b for _, b, _ in res]
+    assert blocks[0][0] == 0 and blocks[-1][1] == len(want)
+    assert all(a[1] == b[0] for a, b in zip(blocks, blocks[1:]))
+    for _, _, got in res:
+        assert got == want
+
+
 def _rank_rows(rank, world, port, out):
     dist = _init(rank, world, port)
     from oracle import oracle as O
