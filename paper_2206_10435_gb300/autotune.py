@@ -24,6 +24,28 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 CANDIDATES = (1, 2, 4, 8, 16)
 
 
+def _load_cache(path, use):
+    """The cache file's entries ({} when unused, missing or unreadable)."""
+    if use and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+            return cache if isinstance(cache, dict) else {}
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store_cache(path, cache):
+    """Writes the cache through a temporary file renamed over the old one, so
+    a reader never sees a partial file."""
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+
+
 def signature(batch, gpu_name: str) -> str:
     rows = 0 if batch.n_rows <= 0 else int(round(math.log2(batch.n_rows)))
     return f"{gpu_name}|rows2^{rows}|rel{batch.n_relations}|lv{batch.levels}|bits{batch.key_bits}"
@@ -34,12 +56,7 @@ def tune_batch(batch, candidates=CANDIDATES, reps: int = 3, cache_path: str = DE
     import torch
     gpu = torch.cuda.get_device_name(batch.ctx.device)
     key = signature(batch, gpu)
-    cache = {}
-    if use_cache and os.path.exists(cache_path):
-        try:
-            cache = json.load(open(cache_path))
-        except (OSError, ValueError):
-            cache = {}
+    cache = _load_cache(cache_path, use_cache)
     if use_cache and key in cache:
         batch.set_grid_mult(int(cache[key]["grid_mult"]))
         return dict(cache[key], cached=True)
@@ -61,10 +78,7 @@ def tune_batch(batch, candidates=CANDIDATES, reps: int = 3, cache_path: str = DE
     entry = {"grid_mult": best, "ms": times[best], "candidates_ms": {str(k): v for k, v in times.items()}}
     if use_cache:
         cache[key] = entry
-        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
-        tmp = cache_path + f".{os.getpid()}.tmp"
-        json.dump(cache, open(tmp, "w"), indent=1)
-        os.replace(tmp, cache_path)
+        _store_cache(cache_path, cache)
     return dict(entry, cached=False)
 
 
@@ -100,12 +114,7 @@ def tune_emit(ctx, query, window: int = 1 << 24, reps: int = 3, cache_path: str 
         return {"rpt": 4, "skipped": "empty result"}
     n = min(window, total)
     key = emit_signature(query, gpu, n)
-    cache = {}
-    if use_cache and os.path.exists(cache_path):
-        try:
-            cache = json.load(open(cache_path))
-        except (OSError, ValueError):
-            cache = {}
+    cache = _load_cache(cache_path, use_cache)
     if use_cache and key in cache:
         ctx.set_option(gj.GJ_OPT_EMIT_ROWS_PER_THREAD, int(cache[key]["rpt"]))
         return dict(cache[key], cached=True)
@@ -128,10 +137,7 @@ def tune_emit(ctx, query, window: int = 1 << 24, reps: int = 3, cache_path: str 
     entry = {"rpt": best, "ms": times[best], "candidates_ms": {str(k): v for k, v in times.items()}}
     if use_cache:
         cache[key] = entry
-        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
-        tmp = cache_path + f".{os.getpid()}.tmp"
-        json.dump(cache, open(tmp, "w"), indent=1)
-        os.replace(tmp, cache_path)
+        _store_cache(cache_path, cache)
     return dict(entry, cached=False)
 
 
@@ -141,22 +147,6 @@ def summary_signature(query, gpu_name: str, kind: str) -> str:
     g2 = "-".join(str(int(round(math.log2(g)))) for g in groups)
     tree = "-".join(str(p) for p in query.parent)
     return f"{gpu_name}|summary|{kind}|rel{query.n_rel}|groups2^{g2}|parents{tree}"
-
-
-def _load_cache(path, use):
-    if use and os.path.exists(path):
-        try:
-            return json.load(open(path))
-        except (OSError, ValueError):
-            return {}
-    return {}
-
-
-def _store_cache(path, cache):
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    tmp = path + f".{os.getpid()}.tmp"
-    json.dump(cache, open(tmp, "w"), indent=1)
-    os.replace(tmp, path)
 
 
 def tune_summary(ctx, query, triangle: bool = False, reps: int = 3, cache_path: str = DEFAULT_CACHE,
