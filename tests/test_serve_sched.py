@@ -1,5 +1,7 @@
 """Scheduler of the serving loop, with a fake engine (no GPU): admission
-under the memory budget, FIFO order, slot concurrency, rejection."""
+under the memory budget, FIFO order, slot concurrency, rejection; the
+latency statistics of the native server's results and the Poisson arrival
+process of the serving benchmark."""
 import threading
 import time
 
@@ -73,3 +75,32 @@ def test_poisson_stream_and_stats():
     reqs = run_stream(srv, list(range(50)), offs)
     st = latency_stats(reqs)
     assert st["completed"] == 50 and st["p99_first_chunk_ms"] >= st["p50_first_chunk_ms"] > 0
+
+
+def test_native_stats_of_known_times():
+    from paper_2206_10435_gb300.serve import native_latency_stats
+    # request i arrives at i ms; summary +1 ms, first chunk +2 ms, last chunk
+    # +(3 + i % 4) ms; every 10th request failed (status 3, out of memory),
+    # request 5 overflowed (status 4, still answered)
+    res = []
+    for i in range(100):
+        t = i / 1000.0
+        res.append({"status": 3 if i % 10 == 9 else (4 if i == 5 else 0), "t_arrival": t,
+                    "t_summary": t + 0.001, "t_chunk": t + 0.002, "t_last": t + (3 + i % 4) / 1000.0,
+                    "rows": 10})
+    st = native_latency_stats(res)
+    assert st["completed"] == 90 and st["failed"] == 10 and st["rows_streamed"] == 900
+    assert abs(st["p50_summary_ms"] - 1.0) < 1e-9 and abs(st["p99_first_chunk_ms"] - 2.0) < 1e-9
+    assert 3.0 <= st["p50_last_chunk_ms"] <= 6.0 and abs(st["p99_last_chunk_ms"] - 6.0) < 1e-9
+    # the span runs from the first arrival (0 ms) to the last finished chunk
+    # of a completed request (request 98: 98 + 5 ms)
+    assert abs(st["qps"] - 90 / 0.103) < 1e-6 and abs(st["rows_per_s"] - 900 / 0.103) < 1e-6
+    assert native_latency_stats([dict(res[9])]) == {"completed": 0}
+
+
+def test_poisson_arrivals_have_the_offered_rate():
+    offs = poisson_arrivals(1000.0, 20_000, seed=3)
+    gaps = offs[1:] - offs[:-1]
+    assert (gaps > 0).all()
+    assert abs(offs[-1] / 20_000 - 1e-3) < 3e-5            # mean gap within 3%
+    assert abs(gaps.std() / gaps.mean() - 1.0) < 0.05      # exponential: sd = mean
